@@ -1,0 +1,148 @@
+/*
+ * grav.h - C ABI of the GB300 fast forward library for gravity (gz) and the
+ * gravity-gradient tensor (gxx, gxy, gxz, gyy, gyz, gzz) of a right-prism
+ * density mesh observed on a horizontal plane.
+ *
+ * Method (Cao, "Rapid forward of gravity and tensor gravity data"):
+ *   d = G M (Eqs. 3-4).  By translation equivalence (Eq. 7, Eq. 10) each
+ *   depth layer's block of G is block Toeplitz with Toeplitz blocks
+ *   (Sec. 2.2.3, Eqs. 17 and 20), fixed by its (2nx-1)(2ny-1) offset values;
+ *   the product with a layer of densities is a circulant embedding plus FFT
+ *   (Eqs. 18-19), and the layers add up (Eq. 21).  The plan stores only the
+ *   kernel spectra (Eq. 22) instead of G.
+ *
+ * Geometry (Fig. 1; cell order j = l + nx m + nx ny n, Sec. 2.2):
+ *   z is positive down.  Cell (l, m, n) spans [l dx, (l+1) dx] x
+ *   [m dy, (m+1) dy] x [n dz, (n+1) dz].  Station (p, q) is at
+ *   ((p + 1/2) dx, (q + 1/2) dy, -h) with h > 0: one station above every
+ *   column of cells.  Units are SI: density kg/m^3, gz m/s^2, gradients 1/s^2;
+ *   the gravitational constant is 6.672e-11 (Sec. 2.1).
+ *
+ * Layouts (row-major, x fastest):
+ *   rho  [nz][ny][nx]      density (forward input)
+ *   out  [ncomp][ny][nx]   one plane per selected component, in ascending
+ *                          bit order of the component mask
+ *   r    [ncomp][ny][nx]   residual / data-space vector (adjoint input)
+ *   grad [nz][ny][nx]      G^T r (adjoint output)
+ *   Element type: float, or double when GRAV_FP64_SPECTRAL is set.
+ *
+ * Ownership and ordering: the caller owns every device buffer passed in;
+ * the plan owns its kernel spectra and workspaces.  grav_forward and
+ * grav_adjoint are asynchronous on the given CUDA stream (NULL = legacy
+ * default stream) and never synchronise on success.  One plan runs one
+ * call at a time: calls on different streams that overlap on the device
+ * share the plan's workspaces and race.  Every entry point may be called
+ * from any host thread; the error message is thread-local.
+ *
+ * Errors: entry points returning int give GRAV_OK (0) or a negative code;
+ * grav_plan_create returns NULL on error.  grav_last_error() then holds a
+ * message.  Invalid arguments never touch the device.
+ */
+#ifndef GRAV_H
+#define GRAV_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct grav_plan grav_plan;
+
+/* Component mask bits (Eq. 1): the five independent gradient components,
+ * gz (Eq. 2) and the derived gzz = -(gxx + gyy). */
+enum {
+    GRAV_GZ = 1,
+    GRAV_GXX = 2,
+    GRAV_GXY = 4,
+    GRAV_GXZ = 8,
+    GRAV_GYY = 16,
+    GRAV_GYZ = 32,
+    GRAV_GZZ = 64,
+    GRAV_ALL6 = 63,
+    /* Precision flag: FP64 input, spectra, FFTs and output.  Without it the
+     * spectra are stored as FP32 and the per-call arithmetic is FP32 with a
+     * compensated (Kahan) sum over the depth layers. */
+    GRAV_FP64_SPECTRAL = 1 << 16
+};
+
+/* Status codes. */
+enum {
+    GRAV_OK = 0,
+    GRAV_EINVAL = -1,   /* bad size, spacing, height, mask or null pointer */
+    GRAV_ENOMEM = -2,   /* device memory (HBM) exhausted */
+    GRAV_ECUDA = -3,    /* a CUDA call failed; the message names it */
+    GRAV_ETIMEOUT = -4  /* reserved: a bounded device wait gave up */
+};
+
+/* Limits of this implementation. */
+#define GRAV_MAX_NX 2048
+#define GRAV_MAX_NY 1024
+
+/* Build a plan: generate the kernel of every layer over the offset grid in
+ * FP64 (Eq. 2 and the gradient closed forms, translation form Eq. 10),
+ * embed it in a circulant (Eq. 19), transform it and keep the spectra
+ * resident on the current device (Eq. 22).  Blocks until done.
+ *   nx, ny, nz  cells per axis: 1 <= nx <= GRAV_MAX_NX, 1 <= ny <= GRAV_MAX_NY,
+ *               nz >= 1
+ *   dx, dy, dz  cell size in metres, > 0
+ *   h           station height above the mesh top in metres, > 0
+ *   components  OR of GRAV_GZ ... GRAV_GZZ, optionally | GRAV_FP64_SPECTRAL
+ * Returns NULL on error (GRAV_EINVAL or GRAV_ENOMEM class, see
+ * grav_last_error). */
+grav_plan* grav_plan_create(int nx, int ny, int nz, double dx, double dy, double dz,
+                            double h, unsigned components);
+
+/* Forward d_c = sum_n G_{c,n} rho_n (Eq. 21) for every selected component.
+ *   rho_dev  device [nz][ny][nx], float (double with GRAV_FP64_SPECTRAL)
+ *   out_dev  device [ncomp][ny][nx], same type; fully overwritten
+ *   stream   cudaStream_t or NULL
+ * Returns GRAV_OK, GRAV_EINVAL (null plan or pointer) or GRAV_ECUDA. */
+int grav_forward(grav_plan* plan, const void* rho_dev, void* out_dev, void* stream);
+
+/* Adjoint grad = sum_c G_c^T r_c: the transpose of Eq. 21, a per-layer
+ * product with the conjugate kernel spectra and no sum over layers.
+ *   r_dev     device [ncomp][ny][nx]
+ *   grad_dev  device [nz][ny][nx]; fully overwritten
+ * Same types, stream and status codes as grav_forward. */
+int grav_adjoint(grav_plan* plan, const void* r_dev, void* grad_dev, void* stream);
+
+/* Release the plan and its device memory (waits for the device first).
+ * NULL is ignored. */
+void grav_plan_destroy(grav_plan* plan);
+
+/* Message of the last failing call on this host thread ("" if none). */
+const char* grav_last_error(void);
+
+/* Device bytes the plan holds (spectra + workspaces + tables): the figure an
+ * HBM-budget admission check needs.  0 for NULL. */
+size_t grav_plan_bytes(const grav_plan* plan);
+
+/* Sizes chosen by the plan. */
+typedef struct {
+    int nx, ny, nz;
+    int px, py;              /* circulant (FFT) sizes per axis, powers of 2 >= 2n-1 */
+    int ncomp;               /* selected components */
+    int fp64;                /* 1 with GRAV_FP64_SPECTRAL */
+    size_t spectra_bytes;    /* resident kernel spectra */
+    size_t workspace_bytes;  /* per-call scratch owned by the plan */
+} grav_plan_info_t;
+
+/* Fill *info.  Returns GRAV_OK or GRAV_EINVAL. */
+int grav_plan_info(const grav_plan* plan, grav_plan_info_t* info);
+
+/* The kernel values themselves (the first row and column of every Toeplitz
+ * block, Eqs. 17 and 19), as the plan generates them in FP64:
+ *   K_dev  device double [ncomp][nz][2ny-1][2nx-1]; entry
+ *          [c][n][v + ny - 1][u + nx - 1] is G_c for a station and the
+ *          cell offset by (u, v) columns in layer n (Eq. 10).
+ * Asynchronous on stream.  Same argument rules as grav_plan_create.
+ * Returns GRAV_OK, GRAV_EINVAL or GRAV_ECUDA. */
+int grav_kernel_values(int nx, int ny, int nz, double dx, double dy, double dz, double h,
+                       unsigned components, double* K_dev, void* stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* GRAV_H */

@@ -16,7 +16,9 @@ Component bits (ascending bit order is the row order of every output):
 from __future__ import annotations
 
 import ctypes
+import hashlib
 import os
+import platform
 import subprocess
 import threading
 
@@ -32,16 +34,29 @@ COMPONENTS = ("gz", "gxx", "gxy", "gxz", "gyy", "gyz", "gzz")
 UPSILON = 6.672e-11
 
 
+_CMD = ["gcc", "-O2", "-std=c11", "-fPIC", "-shared"]
+
+
+def _stamp() -> str:
+    h = hashlib.sha256(platform.machine().encode() + " ".join(_CMD).encode())
+    with open(_SRC, "rb") as fh:
+        h.update(fh.read())
+    return h.hexdigest()
+
+
 def build(force: bool = False) -> str:
-    """Compile ``prism_oracle.c`` into ``_prism_oracle.so`` (plain -O2, IEEE)."""
-    if not force and os.path.exists(_LIB_PATH) and (
-        os.path.getmtime(_LIB_PATH) >= os.path.getmtime(_SRC)
-    ):
-        return _LIB_PATH
+    """Compile ``prism_oracle.c`` into ``_prism_oracle.so`` (plain -O2, IEEE,
+    no fast-math) unless a build for this machine and source exists."""
+    stamp_path = _LIB_PATH + ".stamp"
+    if not force and os.path.exists(_LIB_PATH) and os.path.exists(stamp_path):
+        with open(stamp_path) as fh:
+            if fh.read().strip() == _stamp():
+                return _LIB_PATH
     tmp = _LIB_PATH + f".tmp{os.getpid()}"
-    cmd = ["gcc", "-O2", "-std=c11", "-fPIC", "-shared", "-o", tmp, _SRC, "-lm", "-lpthread"]
-    subprocess.run(cmd, check=True)
+    subprocess.run(_CMD + ["-o", tmp, _SRC, "-lm", "-lpthread"], check=True)
     os.replace(tmp, _LIB_PATH)
+    with open(stamp_path, "w") as fh:
+        fh.write(_stamp())
     return _LIB_PATH
 
 

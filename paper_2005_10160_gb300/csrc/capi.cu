@@ -1,0 +1,388 @@
+// C ABI of the library (include/grav.h): plan construction (kernel
+// generation, circulant embedding and kernel spectra, Eqs. 10, 19, 22) and
+// the per-call forward (Eq. 21) and adjoint pipelines.
+//
+// Forward, per call, on the caller's stream:
+//   1. row transforms of every density row (R2C along x, zero-padded to px),
+//      written column-major per frequency column             [row stage]
+//   2. per (kx, ky parity): column FFT of each layer, multiply by the
+//      kernel spectra, sum over layers, inverse column FFT   [column stage]
+//   3. inverse row transforms (C2R) cropped to the stations  [row stage]
+// The adjoint runs the same three stages in mirror image.
+#include <math.h>
+#include <stdarg.h>
+#include <stdio.h>
+#include <stdlib.h>
+#include <string.h>
+
+#include <new>
+
+#include "grav_internal.h"
+
+namespace grav {
+
+namespace {
+thread_local char g_err[512] = "";
+
+int ilog2(int v) {
+    int l = 0;
+    while ((1 << l) < v) ++l;
+    return l;
+}
+
+// Smallest power of two >= max(4, 2n - 1): the circulant size of one axis
+// (Eq. 19 embeds 2n - 1 kernel values; any size >= 2n - 1 gives the exact
+// product).
+int circulant_size(int n) {
+    int p = 4;
+    while (p < 2 * n - 1) p *= 2;
+    return p;
+}
+
+size_t round_up(size_t v, size_t m) { return (v + m - 1) / m * m; }
+
+// exp(-2 pi i e / T) with exact quadrant symmetry; T is a power of two >= 4.
+void unit_root(long e, long T, double* re, double* im) {
+    e = ((e % T) + T) % T;
+    const long quarter = T / 4;
+    const long q = e / quarter, rr = e - q * quarter;
+    double c, s;
+    if (2 * rr <= quarter) {
+        const double phi = 2.0 * M_PI * (double)rr / (double)T;
+        c = cos(phi);
+        s = sin(phi);
+    } else {
+        const double phi = 2.0 * M_PI * (double)(quarter - rr) / (double)T;
+        c = sin(phi);
+        s = cos(phi);
+    }
+    double ct, st;  // cos and sin of the full angle 2 pi e / T
+    switch (q) {
+        case 0: ct = c; st = s; break;
+        case 1: ct = -s; st = c; break;
+        case 2: ct = -c; st = -s; break;
+        default: ct = s; st = -c; break;
+    }
+    *re = ct;
+    *im = -st;
+}
+
+int check_geometry(int nx, int ny, int nz, double dx, double dy, double dz, double h, unsigned components) {
+    if (nx < 1 || ny < 1 || nz < 1 || nx > GRAV_MAX_NX || ny > GRAV_MAX_NY) {
+        set_error("mesh size %dx%dx%d outside 1..%d x 1..%d x >=1", nx, ny, nz, GRAV_MAX_NX, GRAV_MAX_NY);
+        return GRAV_EINVAL;
+    }
+    if (!(dx > 0) || !(dy > 0) || !(dz > 0) || !isfinite(dx) || !isfinite(dy) || !isfinite(dz)) {
+        set_error("cell sizes must be finite and > 0 (got %g, %g, %g)", dx, dy, dz);
+        return GRAV_EINVAL;
+    }
+    if (!(h > 0) || !isfinite(h)) {
+        set_error("station height h must be finite and > 0 (got %g)", h);
+        return GRAV_EINVAL;
+    }
+    if ((components & 0x7Fu) == 0 || (components & ~(0x7Fu | (unsigned)GRAV_FP64_SPECTRAL))) {
+        set_error("component mask 0x%x selects no component or has unknown bits", components);
+        return GRAV_EINVAL;
+    }
+    if ((size_t)nz * (size_t)ny * (size_t)nx > (size_t)1 << 31) {
+        set_error("mesh has more than 2^31 cells");
+        return GRAV_EINVAL;
+    }
+    return GRAV_OK;
+}
+
+template <typename T>
+int dev_alloc(T** p, size_t bytes, const char* what) {
+    cudaError_t e = cudaMalloc((void**)p, bytes);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        *p = nullptr;
+        set_error("cudaMalloc of %zu bytes for %s failed: %s", bytes, what, cudaGetErrorString(e));
+        return e == cudaErrorMemoryAllocation ? GRAV_ENOMEM : GRAV_ECUDA;
+    }
+    return GRAV_OK;
+}
+
+void free_plan(grav_plan* p) {
+    if (!p) return;
+    cudaFree(p->spec);
+    cudaFree(p->tw);
+    cudaFree(p->ws_a);
+    cudaFree(p->ws_b);
+    delete p;
+}
+
+int build_twiddles(int log_t, int fp64, void** dev, size_t* bytes) {
+    const long T = 1L << log_t;
+    const size_t elem = fp64 ? 16 : 8;
+    *bytes = (size_t)T * elem;
+    unsigned char* host = (unsigned char*)malloc(*bytes);
+    if (!host) {
+        set_error("host allocation of the twiddle table failed");
+        return GRAV_ENOMEM;
+    }
+    for (long e = 0; e < T; ++e) {
+        double re, im;
+        unit_root(e, T, &re, &im);
+        if (fp64) {
+            double* d = (double*)host + 2 * e;
+            d[0] = re; d[1] = im;
+        } else {
+            float* f = (float*)host + 2 * e;
+            f[0] = (float)re; f[1] = (float)im;
+        }
+    }
+    int rc = dev_alloc(dev, *bytes, "twiddle table");
+    if (rc == GRAV_OK) {
+        cudaError_t e = cudaMemcpy(*dev, host, *bytes, cudaMemcpyHostToDevice);
+        if (e != cudaSuccess) rc = cuda_fail(e, "cudaMemcpy(twiddles)");
+    }
+    free(host);
+    return rc;
+}
+
+template <typename R>
+int make_spectra(grav_plan* p) {
+    // FP64 staging: the embedded kernels of a chunk of layers and their row
+    // transforms, bounded to about 2 GB.
+    const size_t per_layer = (size_t)p->ncomp * p->py * p->px * sizeof(double) +
+                             (size_t)p->kx_count * p->ncomp * p->py * 2 * sizeof(double);
+    const size_t budget = (size_t)2 << 30;
+    int nzc = (int)(budget / per_layer);
+    if (nzc < 1) nzc = 1;
+    if (nzc > p->nz) nzc = p->nz;
+    if (nzc * p->ncomp > 65535) nzc = 65535 / p->ncomp;
+
+    void* tw64 = nullptr;
+    size_t tw64_bytes = 0;
+    int rc = GRAV_OK;
+    if (p->fp64) {
+        tw64 = p->tw;
+    } else {
+        rc = build_twiddles(p->log_t, 1, &tw64, &tw64_bytes);
+        if (rc) return rc;
+    }
+    double* E = nullptr;
+    void* Ehat = nullptr;
+    const size_t e_bytes = (size_t)nzc * p->ncomp * p->py * p->px * sizeof(double);
+    const size_t eh_bytes = (size_t)p->kx_count * nzc * p->ncomp * p->py * 2 * sizeof(double);
+    if ((rc = dev_alloc(&E, e_bytes, "kernel staging")) == GRAV_OK &&
+        (rc = dev_alloc(&Ehat, eh_bytes, "kernel row-transform staging")) == GRAV_OK) {
+        cudaStream_t s;
+        cudaError_t ce = cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking);
+        if (ce != cudaSuccess) {
+            rc = cuda_fail(ce, "cudaStreamCreate");
+        } else {
+            Geometry g{p->nx, p->ny, p->nz, p->dx, p->dy, p->dz, p->h};
+            const double scale = 1.0 / ((double)p->px * (double)p->py);
+            for (int n0 = 0; n0 < p->nz && rc == GRAV_OK; n0 += nzc) {
+                const int n1 = n0 + nzc < p->nz ? n0 + nzc : p->nz;
+                const int cnt = n1 - n0;
+                const int O = cnt * p->ncomp;
+                if ((ce = cudaMemsetAsync(E, 0, (size_t)O * p->py * p->px * sizeof(double), s)) != cudaSuccess) {
+                    rc = cuda_fail(ce, "cudaMemsetAsync(kernel staging)");
+                    break;
+                }
+                if ((ce = launch_kernel_gen(g, p->comps, n0, n1, 0, p->px, p->py, E, s)) != cudaSuccess) {
+                    rc = cuda_fail(ce, "kernel generation launch");
+                    break;
+                }
+                // rows o = slot * cnt + (n - n0) of length px, py of them per o
+                if ((ce = launch_row_r2c<double>(p->log_px, E, (size_t)p->py * p->px, (size_t)p->px, p->px, p->py, O,
+                                                 Ehat, p->py, tw64, p->log_t, s)) != cudaSuccess) {
+                    rc = cuda_fail(ce, "kernel row transform launch");
+                    break;
+                }
+                if ((ce = launch_spec_extract<R>(p->log_py - 1, Ehat, p->kx_count, cnt, p->ncomp, n0, p->nz, p->jp,
+                                                 p->imag_mask, scale, (R*)p->spec, tw64, p->log_t, s)) != cudaSuccess) {
+                    rc = cuda_fail(ce, "kernel spectra launch");
+                    break;
+                }
+            }
+            ce = cudaStreamSynchronize(s);
+            if (rc == GRAV_OK && ce != cudaSuccess) rc = cuda_fail(ce, "plan construction");
+            cudaStreamDestroy(s);
+        }
+    }
+    cudaFree(E);
+    cudaFree(Ehat);
+    if (!p->fp64) cudaFree(tw64);
+    return rc;
+}
+
+template <typename R>
+int run_forward(grav_plan* p, const void* rho, void* out, cudaStream_t s) {
+    cudaError_t e;
+    e = launch_row_r2c<R>(p->log_px, (const R*)rho, (size_t)p->ny * p->nx, (size_t)p->nx, p->nx, p->ny, p->nz, p->ws_a,
+                          p->ny_pad, p->tw, p->log_t, s);
+    if (e != cudaSuccess) return cuda_fail(e, "forward row transform");
+    ColumnArgs a{p->ny, p->ny_pad, p->nz, p->ncomp, p->kx_count, p->jp, p->imag_mask, p->oddv_mask,
+                 p->log_t - (p->log_py - 1), p->log_t - p->log_py};
+    e = launch_forward_columns<R>(p->log_py - 1, a, p->ws_a, (const R*)p->spec, p->ws_b, p->tw, s);
+    if (e != cudaSuccess) return cuda_fail(e, "forward column stage");
+    const size_t half = (size_t)p->kx_count * p->ncomp * p->ny_pad * 2 * sizeof(R);
+    e = launch_row_c2r<R>(p->log_px, p->ws_b, (const unsigned char*)p->ws_b + half, p->ny, p->ncomp, p->ny_pad, (R*)out,
+                          (size_t)p->nx, p->nx, p->tw, p->log_t, s);
+    if (e != cudaSuccess) return cuda_fail(e, "forward inverse row transform");
+    return GRAV_OK;
+}
+
+template <typename R>
+int run_adjoint(grav_plan* p, const void* r, void* grad, cudaStream_t s) {
+    cudaError_t e;
+    e = launch_row_r2c<R>(p->log_px, (const R*)r, (size_t)p->ny * p->nx, (size_t)p->nx, p->nx, p->ny, p->ncomp,
+                          p->ws_b, p->ny_pad, p->tw, p->log_t, s);
+    if (e != cudaSuccess) return cuda_fail(e, "adjoint row transform");
+    ColumnArgs a{p->ny, p->ny_pad, p->nz, p->ncomp, p->kx_count, p->jp, p->imag_mask, p->oddv_mask,
+                 p->log_t - (p->log_py - 1), p->log_t - p->log_py};
+    e = launch_adjoint_columns<R>(p->log_py - 1, a, p->ws_b, (const R*)p->spec, p->ws_a, p->tw, s);
+    if (e != cudaSuccess) return cuda_fail(e, "adjoint column stage");
+    const size_t half = (size_t)p->kx_count * p->nz * p->ny_pad * 2 * sizeof(R);
+    e = launch_row_c2r<R>(p->log_px, p->ws_a, (const unsigned char*)p->ws_a + half, p->ny, p->nz, p->ny_pad, (R*)grad,
+                          (size_t)p->nx, p->nx, p->tw, p->log_t, s);
+    if (e != cudaSuccess) return cuda_fail(e, "adjoint inverse row transform");
+    return GRAV_OK;
+}
+
+}  // namespace
+
+void set_error(const char* fmt, ...) {
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(g_err, sizeof g_err, fmt, ap);
+    va_end(ap);
+}
+
+int cuda_fail(cudaError_t e, const char* what) {
+    set_error("%s: %s", what, cudaGetErrorString(e));
+    return e == cudaErrorMemoryAllocation ? GRAV_ENOMEM : GRAV_ECUDA;
+}
+
+}  // namespace grav
+
+using namespace grav;
+
+extern "C" {
+
+const char* grav_last_error(void) { return g_err; }
+
+grav_plan* grav_plan_create(int nx, int ny, int nz, double dx, double dy, double dz, double h, unsigned components) {
+    g_err[0] = 0;
+    if (check_geometry(nx, ny, nz, dx, dy, dz, h, components)) return nullptr;
+    grav_plan* p = new (std::nothrow) grav_plan;
+    if (!p) {
+        set_error("host allocation of the plan failed");
+        return nullptr;
+    }
+    memset(p, 0, sizeof *p);
+    p->nx = nx; p->ny = ny; p->nz = nz;
+    p->dx = dx; p->dy = dy; p->dz = dz; p->h = h;
+    p->comps = components & 0x7Fu;
+    p->fp64 = (components & GRAV_FP64_SPECTRAL) ? 1 : 0;
+    for (int c = 0; c < kMaxComp; ++c) {
+        if (p->comps & (1u << c)) {
+            const int s = p->ncomp++;
+            p->comp_id[s] = c;
+            if (odd_u(c) != odd_v(c)) p->imag_mask |= 1u << s;
+            if (odd_v(c)) p->oddv_mask |= 1u << s;
+        }
+    }
+    p->px = circulant_size(nx);
+    p->py = circulant_size(ny);
+    p->log_px = ilog2(p->px);
+    p->log_py = ilog2(p->py);
+    p->log_t = p->log_px > p->log_py ? p->log_px : p->log_py;
+    p->kx_count = p->px / 2 + 1;
+    p->J = p->py / 4;
+    p->jp = (int)round_up((size_t)p->J + 1, 4);
+    p->ny_pad = (int)round_up((size_t)ny, 4);
+    cudaGetDevice(&p->device);
+
+    const size_t real = p->fp64 ? sizeof(double) : sizeof(float);
+    p->spec_bytes = (size_t)2 * p->kx_count * nz * p->ncomp * p->jp * real;
+    p->ws_a_bytes = (size_t)2 * p->kx_count * nz * p->ny_pad * 2 * real;
+    p->ws_b_bytes = (size_t)2 * p->kx_count * p->ncomp * p->ny_pad * 2 * real;
+
+    size_t free_b = 0, total_b = 0;
+    cudaError_t ce = cudaMemGetInfo(&free_b, &total_b);
+    if (ce != cudaSuccess) {
+        cuda_fail(ce, "cudaMemGetInfo");
+        delete p;
+        return nullptr;
+    }
+    const size_t need = p->spec_bytes + p->ws_a_bytes + p->ws_b_bytes;
+    if (need > free_b) {
+        set_error("plan needs %zu bytes of device memory, %zu free", need, free_b);
+        delete p;
+        return nullptr;
+    }
+    int rc = build_twiddles(p->log_t, p->fp64, &p->tw, &p->tw_bytes);
+    if (!rc) rc = dev_alloc(&p->spec, p->spec_bytes, "kernel spectra");
+    if (!rc) rc = dev_alloc(&p->ws_a, p->ws_a_bytes, "workspace A");
+    if (!rc) rc = dev_alloc(&p->ws_b, p->ws_b_bytes, "workspace B");
+    if (!rc) rc = p->fp64 ? make_spectra<double>(p) : make_spectra<float>(p);
+    if (rc) {
+        free_plan(p);
+        return nullptr;
+    }
+    return p;
+}
+
+int grav_forward(grav_plan* plan, const void* rho_dev, void* out_dev, void* stream) {
+    if (!plan || !rho_dev || !out_dev) {
+        set_error("grav_forward: null plan or buffer");
+        return GRAV_EINVAL;
+    }
+    cudaStream_t s = (cudaStream_t)stream;
+    return plan->fp64 ? run_forward<double>(plan, rho_dev, out_dev, s) : run_forward<float>(plan, rho_dev, out_dev, s);
+}
+
+int grav_adjoint(grav_plan* plan, const void* r_dev, void* grad_dev, void* stream) {
+    if (!plan || !r_dev || !grad_dev) {
+        set_error("grav_adjoint: null plan or buffer");
+        return GRAV_EINVAL;
+    }
+    cudaStream_t s = (cudaStream_t)stream;
+    return plan->fp64 ? run_adjoint<double>(plan, r_dev, grad_dev, s) : run_adjoint<float>(plan, r_dev, grad_dev, s);
+}
+
+void grav_plan_destroy(grav_plan* plan) {
+    if (!plan) return;
+    cudaDeviceSynchronize();
+    free_plan(plan);
+}
+
+size_t grav_plan_bytes(const grav_plan* plan) {
+    if (!plan) return 0;
+    return plan->spec_bytes + plan->tw_bytes + plan->ws_a_bytes + plan->ws_b_bytes;
+}
+
+int grav_plan_info(const grav_plan* plan, grav_plan_info_t* info) {
+    if (!plan || !info) {
+        set_error("grav_plan_info: null argument");
+        return GRAV_EINVAL;
+    }
+    info->nx = plan->nx; info->ny = plan->ny; info->nz = plan->nz;
+    info->px = plan->px; info->py = plan->py;
+    info->ncomp = plan->ncomp;
+    info->fp64 = plan->fp64;
+    info->spectra_bytes = plan->spec_bytes;
+    info->workspace_bytes = plan->ws_a_bytes + plan->ws_b_bytes;
+    return GRAV_OK;
+}
+
+int grav_kernel_values(int nx, int ny, int nz, double dx, double dy, double dz, double h, unsigned components,
+                       double* K_dev, void* stream) {
+    int rc = check_geometry(nx, ny, nz, dx, dy, dz, h, components);
+    if (rc) return rc;
+    if (!K_dev) {
+        set_error("grav_kernel_values: null output");
+        return GRAV_EINVAL;
+    }
+    Geometry g{nx, ny, nz, dx, dy, dz, h};
+    cudaError_t e = launch_kernel_gen(g, components & 0x7Fu, 0, nz, 1, 0, 0, K_dev, (cudaStream_t)stream);
+    if (e != cudaSuccess) return cuda_fail(e, "kernel generation launch");
+    return GRAV_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,154 @@
+// Shared-memory FFT building blocks for the spectral BTTB product.
+//
+// The Toeplitz (Eq. 17) and BTTB (Eq. 20) matrix-vector products are formed
+// by circulant embedding and FFT (Eqs. 18-19).  These device routines run the
+// FFTs inside the calling kernel: complex radix-2/4/8 butterflies in
+// registers, Stockham autosort passes (natural order in and out) through one
+// padded shared-memory buffer, twiddles read from a per-plan table
+// W_T[e] = exp(-2 pi i e / T) with T the largest transform size of the plan.
+//
+// Conventions: forward transforms use exp(-2 pi i jk/N), inverse ones
+// exp(+2 pi i jk/N); neither is normalised (the 1/(Px Py) of the inverse is
+// folded into the stored kernel spectra).
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace grav {
+
+template <typename R> struct cplx;
+template <> struct cplx<float> { using type = float2; };
+template <> struct cplx<double> { using type = double2; };
+
+template <typename C> __device__ __forceinline__ C cmk(decltype(C::x) a, decltype(C::x) b) { C c; c.x = a; c.y = b; return c; }
+template <typename C> __device__ __forceinline__ C cadd(C a, C b) { return cmk<C>(a.x + b.x, a.y + b.y); }
+template <typename C> __device__ __forceinline__ C csub(C a, C b) { return cmk<C>(a.x - b.x, a.y - b.y); }
+template <typename C> __device__ __forceinline__ C cmul(C a, C b) {
+    return cmk<C>(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
+}
+template <typename C> __device__ __forceinline__ C cconj(C a) { return cmk<C>(a.x, -a.y); }
+template <typename C> __device__ __forceinline__ C cscale(C a, decltype(C::x) s) { return cmk<C>(a.x * s, a.y * s); }
+// Multiply by -i (forward sign) or +i (inverse sign).
+template <typename C, bool INV> __device__ __forceinline__ C cmul_ni(C a) {
+    return INV ? cmk<C>(-a.y, a.x) : cmk<C>(a.y, -a.x);
+}
+
+// Padded shared-memory index: one spare slot per 128 bytes keeps the
+// strided Stockham stores at (or near) the minimum number of wavefronts.
+template <typename C> __device__ __forceinline__ int sidx(int e) {
+    return e + (e >> (sizeof(C) == 8 ? 4 : 3));
+}
+template <typename C> __host__ __device__ constexpr int spad_len(int n) {
+    return n + (n >> (sizeof(C) == 8 ? 4 : 3)) + 1;
+}
+
+// In-register DFTs of size 2, 4, 8.
+template <typename C, bool INV> __device__ __forceinline__ void dft2(C& a, C& b) {
+    C t = a; a = cadd(t, b); b = csub(t, b);
+}
+template <typename C, bool INV> __device__ __forceinline__ void dft4(C& a0, C& a1, C& a2, C& a3) {
+    C t0 = cadd(a0, a2), t1 = csub(a0, a2);
+    C t2 = cadd(a1, a3), t3 = cmul_ni<C, INV>(csub(a1, a3));
+    a0 = cadd(t0, t2); a2 = csub(t0, t2);
+    a1 = cadd(t1, t3); a3 = csub(t1, t3);
+}
+template <typename C, bool INV> __device__ __forceinline__ void dft8(C* u) {
+    using R = decltype(C::x);
+    const R h = (R)0.70710678118654752440;
+    dft4<C, INV>(u[0], u[2], u[4], u[6]);
+    dft4<C, INV>(u[1], u[3], u[5], u[7]);
+    // odd half times w8^k, w8 = exp(-+ 2 pi i / 8)
+    C o1 = u[3], o2 = u[5], o3 = u[7];
+    C w1 = INV ? cmk<C>(h * (o1.x - o1.y), h * (o1.x + o1.y)) : cmk<C>(h * (o1.x + o1.y), h * (o1.y - o1.x));
+    C w2 = cmul_ni<C, INV>(o2);
+    C w3 = INV ? cmk<C>(-h * (o3.x + o3.y), h * (o3.x - o3.y)) : cmk<C>(h * (o3.y - o3.x), -h * (o3.x + o3.y));
+    C e0 = u[0], e1 = u[2], e2 = u[4], e3 = u[6], o0 = u[1];
+    u[0] = cadd(e0, o0); u[4] = csub(e0, o0);
+    u[1] = cadd(e1, w1); u[5] = csub(e1, w1);
+    u[2] = cadd(e2, w2); u[6] = csub(e2, w2);
+    u[3] = cadd(e3, w3); u[7] = csub(e3, w3);
+}
+template <typename C, int R, bool INV> __device__ __forceinline__ void dftR(C* u) {
+    if constexpr (R == 2) dft2<C, INV>(u[0], u[1]);
+    else if constexpr (R == 4) dft4<C, INV>(u[0], u[1], u[2], u[3]);
+    else dft8<C, INV>(u);
+}
+
+// Radix of pass p for a 2^LOGN transform: the first pass takes LOGN mod 3
+// (radix 2 or 4), the rest are radix 8.
+__host__ __device__ constexpr int pass_radix(int logn, int p) {
+    return (logn % 3 != 0 && p == 0) ? (1 << (logn % 3)) : 8;
+}
+__host__ __device__ constexpr int num_passes(int logn) {
+    return logn / 3 + (logn % 3 != 0 ? 1 : 0);
+}
+// Product of the radices of the passes before p.
+__host__ __device__ constexpr int pass_ls(int logn, int p) {
+    int ls = 1;
+    for (int q = 0; q < p; ++q) ls *= pass_radix(logn, q);
+    return ls;
+}
+
+// One Stockham pass of radix R over NSEQ sequences of length N = 2^LOGN that
+// sit back to back (stride SSTR padded elements) in shared memory.  Threads
+// tid < NT take butterflies tid, tid + NT, ... and hold them in registers
+// across the barrier, so one buffer suffices.  Every thread of the block
+// calls this (it contains __syncthreads()).
+template <typename C, int LOGN, int R, int NSEQ, int NT, bool INV>
+__device__ __forceinline__ void fft_pass(C* buf, int sstr, int ls, const C* __restrict__ tw, int tw_shift, int tid) {
+    constexpr int N = 1 << LOGN;
+    constexpr int NR = N / R;
+    constexpr int TOTAL = NSEQ * NR;
+    constexpr int BPT = (TOTAL + NT - 1) / NT;
+    C u[BPT][R];
+#pragma unroll
+    for (int b = 0; b < BPT; ++b) {
+        const int g = tid + b * NT;
+        if (tid < NT && g < TOTAL) {
+            const int s = g / NR, i = g - s * NR;
+            const C* x = buf + s * sstr;
+#pragma unroll
+            for (int r = 0; r < R; ++r) u[b][r] = x[sidx<C>(i + r * NR)];
+        }
+    }
+    __syncthreads();
+#pragma unroll
+    for (int b = 0; b < BPT; ++b) {
+        const int g = tid + b * NT;
+        if (tid < NT && g < TOTAL) {
+            const int s = g / NR, i = g - s * NR;
+            const int k = i & (ls - 1);
+            if (ls > 1) {
+                // twiddle W_{ls R}^{r k} = W_N^{r k N / (ls R)}
+                const int step = (k * (N / (ls * R))) << tw_shift;
+#pragma unroll
+                for (int r = 1; r < R; ++r) {
+                    C w = tw[r * step];
+                    if (INV) w.y = -w.y;
+                    u[b][r] = cmul(u[b][r], w);
+                }
+            }
+            dftR<C, R, INV>(u[b]);
+            C* y = buf + s * sstr;
+            const int j = (i - k) * R + k;
+#pragma unroll
+            for (int r = 0; r < R; ++r) y[sidx<C>(j + r * ls)] = u[b][r];
+        }
+    }
+    __syncthreads();
+}
+
+// Full in-place FFT of NSEQ sequences of 2^LOGN points in shared memory
+// (natural order in, natural order out).  tw is W_T with T = N << tw_shift.
+template <typename C, int LOGN, int NSEQ, int NT, bool INV>
+__device__ __forceinline__ void block_fft(C* buf, int sstr, const C* __restrict__ tw, int tw_shift, int tid) {
+    constexpr int NP = num_passes(LOGN);
+    static_assert(NP <= 5, "transform too long");
+    if constexpr (NP > 0) fft_pass<C, LOGN, pass_radix(LOGN, 0), NSEQ, NT, INV>(buf, sstr, pass_ls(LOGN, 0), tw, tw_shift, tid);
+    if constexpr (NP > 1) fft_pass<C, LOGN, pass_radix(LOGN, 1), NSEQ, NT, INV>(buf, sstr, pass_ls(LOGN, 1), tw, tw_shift, tid);
+    if constexpr (NP > 2) fft_pass<C, LOGN, pass_radix(LOGN, 2), NSEQ, NT, INV>(buf, sstr, pass_ls(LOGN, 2), tw, tw_shift, tid);
+    if constexpr (NP > 3) fft_pass<C, LOGN, pass_radix(LOGN, 3), NSEQ, NT, INV>(buf, sstr, pass_ls(LOGN, 3), tw, tw_shift, tid);
+    if constexpr (NP > 4) fft_pass<C, LOGN, pass_radix(LOGN, 4), NSEQ, NT, INV>(buf, sstr, pass_ls(LOGN, 4), tw, tw_shift, tid);
+}
+
+}  // namespace grav

@@ -1,0 +1,123 @@
+// Internal plan structure and kernel launchers of the GB300 forward library.
+#pragma once
+#include <cuda_runtime.h>
+#include <stddef.h>
+#include <stdint.h>
+
+#include "../../include/grav.h"
+
+namespace grav {
+
+constexpr int kMaxComp = 7;
+constexpr double kUpsilon = 6.672e-11;  // gravitational constant of Sec. 2.1
+
+// Parity of each component's kernel under x -> -x and y -> -y (the
+// symmetries of Sec. 2.2): gz, gxx, gxy, gxz, gyy, gyz, gzz.
+// Bit c set = component c is odd in that direction.
+constexpr unsigned kOddUMask = 0x0Cu;  // gxy, gxz
+constexpr unsigned kOddVMask = 0x24u;  // gxy, gyz
+__host__ __device__ constexpr bool odd_u(int c) { return (kOddUMask >> c) & 1u; }
+__host__ __device__ constexpr bool odd_v(int c) { return (kOddVMask >> c) & 1u; }
+
+// Geometry shared by the kernel-generation launches.
+struct Geometry {
+    int nx, ny, nz;
+    double dx, dy, dz, h;
+};
+
+// Layout of the resident kernel spectra.  Column kernels run one CTA per
+// (kx, r) with r the parity of ky; the spectrum of every component is real
+// or purely imaginary and even or odd in ky (exact consequences of the
+// kernel's reflection symmetry), so a CTA needs one real number per
+// mirror pair (ky, Py - ky):
+//   spec[((r * kx_count + kx) * nz + n) * ncomp + c) * jp + q]
+// q < J = Py / 4 is the pair index (ky = 2q + r); for r = 0, q = J holds the
+// Nyquist row ky = Py / 2.  jp = J + 1 rounded up to a multiple of 4.
+
+struct ColumnArgs {
+    int ny;            // valid input / output rows
+    int ny_pad;        // row stride of the workspaces
+    int nz;
+    int ncomp;
+    int kx_count;
+    int jp;
+    unsigned imag_mask;  // bit s: component slot s has an imaginary spectrum
+    unsigned oddv_mask;  // bit s: component slot s is odd in y
+    int tw_shift_n;      // log2(T / N) for the half-length column transform
+    int tw_shift_p;      // log2(T / Py) for the parity fold twiddles
+};
+
+}  // namespace grav
+
+struct grav_plan {
+    int nx, ny, nz;
+    double dx, dy, dz, h;
+    unsigned comps;
+    int fp64;
+    int ncomp;
+    int comp_id[grav::kMaxComp];
+    int log_px, log_py, px, py;
+    int kx_count;  // px / 2 + 1
+    int J, jp;
+    int ny_pad;
+    unsigned imag_mask, oddv_mask;
+    int log_t;      // twiddle table length T = max(px, py)
+    void* spec;     // resident spectra (float or double)
+    void* tw;       // twiddle table in the plan's precision
+    void* ws_a;     // workspace: forward row transforms / adjoint column outputs
+    void* ws_b;     // workspace: forward column outputs / adjoint row transforms
+    size_t spec_bytes, tw_bytes, ws_a_bytes, ws_b_bytes;
+    int device;
+};
+
+namespace grav {
+
+// Thread-local error message and CUDA check helpers (capi.cu).
+void set_error(const char* fmt, ...);
+int cuda_fail(cudaError_t e, const char* what);
+
+// ---- kernel generation (kernel_gen.cu) ----
+// mode 0: embed into a circulant array E[(c * nzc + n) * py + b][a] of size
+//         py x px per (component, layer); E must be zeroed beforehand.
+// mode 1: dense offset grid K[c][n][2ny-1][2nx-1].
+cudaError_t launch_kernel_gen(const Geometry& g, unsigned comps, int n0, int n1, int mode,
+                              int px, int py, double* out, cudaStream_t s);
+
+// ---- row transforms (fft_rows.cu) ----
+// Real rows -> half spectra, written transposed:
+//   in  row (o, i) at in + o * in_ostride + i * in_istride, l_in valid values
+//   out[(kx * O + o) * i_pad + i], kx in [0, P/2]
+template <typename R>
+cudaError_t launch_row_r2c(int log_p, const R* in, size_t in_ostride, size_t in_istride,
+                           int l_in, int I, int O, void* out, int i_pad, const void* tw,
+                           int log_t, cudaStream_t s);
+// Half spectra (the sum of in0 and in1, layout as above) -> real rows:
+//   out row (o, i) at out + (o * I + i) * out_stride, first l_out values.
+template <typename R>
+cudaError_t launch_row_c2r(int log_p, const void* in0, const void* in1, int I, int O, int i_pad,
+                           R* out, size_t out_stride, int l_out, const void* tw, int log_t,
+                           cudaStream_t s);
+
+// ---- column kernels (spectral.cuh, col_*.cu) ----
+template <typename R>
+cudaError_t launch_forward_columns(int log_n, const ColumnArgs& a, const void* X, const R* spec,
+                                   void* Y, const void* tw, cudaStream_t s);
+template <typename R>
+cudaError_t launch_adjoint_columns(int log_n, const ColumnArgs& a, const void* Xr, const R* spec,
+                                   void* Z, const void* tw, cudaStream_t s);
+template <> cudaError_t launch_forward_columns<float>(int, const ColumnArgs&, const void*, const float*, void*,
+                                                     const void*, cudaStream_t);
+template <> cudaError_t launch_forward_columns<double>(int, const ColumnArgs&, const void*, const double*, void*,
+                                                      const void*, cudaStream_t);
+template <> cudaError_t launch_adjoint_columns<float>(int, const ColumnArgs&, const void*, const float*, void*,
+                                                     const void*, cudaStream_t);
+template <> cudaError_t launch_adjoint_columns<double>(int, const ColumnArgs&, const void*, const double*, void*,
+                                                      const void*, cudaStream_t);
+// Column FFT of embedded kernel row transforms and extraction of the stored
+// real numbers.  Ehat[kx][o][b] (b < py, row stride py), o = c * nzc + n.
+template <typename RO>
+cudaError_t launch_spec_extract(int log_n, const void* ehat, int kx_count, int nzc, int ncomp,
+                                int n0, int nz, int jp, unsigned imag_mask, double scale, RO* spec,
+                                const void* tw64, int log_t, cudaStream_t s);
+
+}  // namespace grav

@@ -1,0 +1,114 @@
+// FP64 kernel generation: the translation-equivalent geometric kernel
+// K_c(u, v, n) of every component c over the offset grid (Eq. 10), i.e. the
+// first row and column of every Toeplitz block of G (Eqs. 17, 19).
+//
+// K_c(u, v, n) is the field at a station due to a unit-density cell offset
+// by (u, v) columns in layer n.  With the station at the origin the cell has
+// corners x_i = (1/2 - u) dx, -(1/2 + u) dx, y_j likewise, z_k = -h - zeta_k
+// with zeta in {n dz, (n+1) dz}, and
+//     K_c = upsilon * sum_{ijk} mu_ijk F_c(x_i, y_j, z_k),  mu_ijk = (-1)^(i+j+k)
+// (Eq. 2).  F_c is the closed form of Eq. 2 for gz (its logarithms written
+// as asinh, which is the same function and keeps far offsets accurate) and
+// the standard prism forms for the gradient components:
+//     gxx: atan(yz/(xr))   gyy: atan(xz/(yr))   gzz: atan(xy/(zr))
+//     gxy: -asinh(z/sqrt(x^2+y^2))   gxz: -asinh(y/sqrt(x^2+z^2))
+//     gyz: -asinh(x/sqrt(y^2+z^2))
+// FP64 throughout: the eight corner terms cancel to a few parts in 1e7 at
+// the far offsets of a 1024-cell mesh, so FP32 generation is unusable.
+//
+// One thread per offset (u, v) of the quadrant u, v >= 0.  It walks down the
+// layers keeping the four (x, y)-corner terms of the shared z-level in
+// registers (the bottom of layer n is the top of layer n + 1), and writes
+// the four mirrored offsets (+-u, +-v) using the component's parity under
+// reflection (Sec. 2.2), so the stored kernel is exactly even or odd.
+#include "grav_internal.h"
+
+namespace grav {
+
+namespace {
+
+__device__ __forceinline__ void corner_terms(double x, double y, double z, unsigned comps, double F[kMaxComp]) {
+    const double x2 = x * x, y2 = y * y, z2 = z * z;
+    const double r = sqrt(x2 + y2 + z2);
+    double ay = 0.0, ax = 0.0, az = 0.0, tz = 0.0, tx = 0.0, ty = 0.0;
+    if (comps & (GRAV_GZ | GRAV_GXZ)) ay = asinh(y / sqrt(x2 + z2));
+    if (comps & (GRAV_GZ | GRAV_GYZ)) ax = asinh(x / sqrt(y2 + z2));
+    if (comps & GRAV_GXY) az = asinh(z / sqrt(x2 + y2));
+    if (comps & (GRAV_GZ | GRAV_GZZ)) tz = atan(x * y / (z * r));
+    if (comps & GRAV_GXX) tx = atan(y * z / (x * r));
+    if (comps & GRAV_GYY) ty = atan(x * z / (y * r));
+    F[0] = -(x * ay + y * ax - z * tz);
+    F[1] = tx;
+    F[2] = -az;
+    F[3] = -ay;
+    F[4] = ty;
+    F[5] = -ax;
+    F[6] = tz;
+}
+
+__global__ void kernel_gen(Geometry g, unsigned comps, int n0, int n1, int mode, int px, int py, double* __restrict__ out) {
+    const int u = blockIdx.x * blockDim.x + threadIdx.x;
+    const int v = blockIdx.y;
+    if (u >= g.nx || v >= g.ny) return;
+    const double xs[2] = {(0.5 - u) * g.dx, -(0.5 + u) * g.dx};
+    const double ys[2] = {(0.5 - v) * g.dy, -(0.5 + v) * g.dy};
+
+    double top[4][kMaxComp];
+    {
+        const double z = -g.h - n0 * g.dz;
+#pragma unroll
+        for (int ij = 0; ij < 4; ++ij) corner_terms(xs[ij >> 1], ys[ij & 1], z, comps, top[ij]);
+    }
+    const int nzc = n1 - n0;
+    const int wx = 2 * g.nx - 1, wy = 2 * g.ny - 1;
+    for (int n = n0; n < n1; ++n) {
+        double bot[4][kMaxComp];
+        const double z = -g.h - (n + 1) * g.dz;
+#pragma unroll
+        for (int ij = 0; ij < 4; ++ij) corner_terms(xs[ij >> 1], ys[ij & 1], z, comps, bot[ij]);
+#pragma unroll
+        for (int c = 0; c < kMaxComp; ++c) {
+            if (!(comps & (1u << c))) continue;
+            const int s = __popc(comps & ((1u << c) - 1u));  // output slot of component c
+            // mu_ijk: +1 for the bottom z-level when i + j is even
+            const double d00 = bot[0][c] - top[0][c];
+            const double d01 = bot[1][c] - top[1][c];
+            const double d10 = bot[2][c] - top[2][c];
+            const double d11 = bot[3][c] - top[3][c];
+            const double K = kUpsilon * ((d00 - d01) - (d10 - d11));
+            for (int mu = 0; mu < (u > 0 ? 2 : 1); ++mu) {
+                for (int mv = 0; mv < (v > 0 ? 2 : 1); ++mv) {
+                    double val = K;
+                    if (mu && odd_u(c)) val = -val;
+                    if (mv && odd_v(c)) val = -val;
+                    if ((u == 0 && odd_u(c)) || (v == 0 && odd_v(c))) val = 0.0;
+                    const int U = mu ? -u : u, V = mv ? -v : v;
+                    size_t idx;
+                    if (mode == 0) {
+                        const int a = (px - U) & (px - 1), b = (py - V) & (py - 1);
+                        idx = (((size_t)s * nzc + (n - n0)) * py + b) * px + a;
+                    } else {
+                        idx = (((size_t)s * g.nz + n) * wy + (V + g.ny - 1)) * wx + (U + g.nx - 1);
+                    }
+                    out[idx] = val;
+                }
+            }
+        }
+#pragma unroll
+        for (int ij = 0; ij < 4; ++ij)
+#pragma unroll
+            for (int c = 0; c < kMaxComp; ++c) top[ij][c] = bot[ij][c];
+    }
+}
+
+}  // namespace
+
+cudaError_t launch_kernel_gen(const Geometry& g, unsigned comps, int n0, int n1, int mode, int px, int py,
+                              double* out, cudaStream_t s) {
+    const int bx = 64;
+    dim3 grid((g.nx + bx - 1) / bx, g.ny);
+    kernel_gen<<<grid, bx, 0, s>>>(g, comps & 0x7Fu, n0, n1, mode, px, py, out);
+    return cudaGetLastError();
+}
+
+}  // namespace grav

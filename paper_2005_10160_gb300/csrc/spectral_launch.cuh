@@ -1,0 +1,58 @@
+// Launch helpers for the column kernels: one template instance per
+// (transform length, components per thread group).
+#pragma once
+#include "spectral.cuh"
+
+namespace grav {
+
+template <typename R, int LOGN, int CPG>
+cudaError_t forward_impl(const ColumnArgs& a, const void* X, const R* spec, void* Y, const void* tw, cudaStream_t s) {
+    using C = typename cplx<R>::type;
+    constexpr bool KAHAN = sizeof(R) == 4;
+    auto k = forward_column_kernel<R, LOGN, CPG, KAHAN>;
+    const size_t smem = column_smem_bytes<R>(LOGN);
+    cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    k<<<dim3(a.kx_count, 2), ColShape<LOGN>::NT, smem, s>>>(a, (const C*)X, spec, (C*)Y, (const C*)tw);
+    return cudaGetLastError();
+}
+
+template <typename R, int LOGN, int CPG>
+cudaError_t adjoint_impl(const ColumnArgs& a, const void* Xr, const R* spec, void* Z, const void* tw, cudaStream_t s) {
+    using C = typename cplx<R>::type;
+    auto k = adjoint_column_kernel<R, LOGN, CPG>;
+    const size_t smem = column_smem_bytes<R>(LOGN);
+    cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    k<<<dim3(a.kx_count, 2), ColShape<LOGN>::NT, smem, s>>>(a, (const C*)Xr, spec, (C*)Z, (const C*)tw);
+    return cudaGetLastError();
+}
+
+#define GRAV_CPG_SWITCH(FN, R, L, ...)                       \
+    switch (cpg_for(a.ncomp)) {                              \
+        case 1: return FN<R, L, 1>(__VA_ARGS__);             \
+        case 2: return FN<R, L, 2>(__VA_ARGS__);             \
+        case 3: return FN<R, L, 3>(__VA_ARGS__);             \
+        default: return FN<R, L, 4>(__VA_ARGS__);            \
+    }
+
+#define GRAV_COLUMN_LAUNCHER(NAME, IMPL, R)                                                              \
+    template <>                                                                                          \
+    cudaError_t NAME<R>(int log_n, const ColumnArgs& a, const void* in, const R* spec, void* out,       \
+                        const void* tw, cudaStream_t s) {                                                \
+        switch (log_n) {                                                                                 \
+            case 1: GRAV_CPG_SWITCH(IMPL, R, 1, a, in, spec, out, tw, s)                                 \
+            case 2: GRAV_CPG_SWITCH(IMPL, R, 2, a, in, spec, out, tw, s)                                 \
+            case 3: GRAV_CPG_SWITCH(IMPL, R, 3, a, in, spec, out, tw, s)                                 \
+            case 4: GRAV_CPG_SWITCH(IMPL, R, 4, a, in, spec, out, tw, s)                                 \
+            case 5: GRAV_CPG_SWITCH(IMPL, R, 5, a, in, spec, out, tw, s)                                 \
+            case 6: GRAV_CPG_SWITCH(IMPL, R, 6, a, in, spec, out, tw, s)                                 \
+            case 7: GRAV_CPG_SWITCH(IMPL, R, 7, a, in, spec, out, tw, s)                                 \
+            case 8: GRAV_CPG_SWITCH(IMPL, R, 8, a, in, spec, out, tw, s)                                 \
+            case 9: GRAV_CPG_SWITCH(IMPL, R, 9, a, in, spec, out, tw, s)                                 \
+            case 10: GRAV_CPG_SWITCH(IMPL, R, 10, a, in, spec, out, tw, s)                               \
+            default: return cudaErrorInvalidValue;                                                       \
+        }                                                                                                \
+    }
+
+}  // namespace grav

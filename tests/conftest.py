@@ -18,3 +18,23 @@ def orc():
 
     oracle.build()
     return oracle
+
+
+@pytest.fixture(scope="session")
+def gravlib():
+    """Build (if stale) and load libgravfft.so."""
+    from paper_2005_10160_gb300 import build, capi
+
+    build.build()
+    return capi.lib()
+
+
+def pytest_collection_modifyitems(config, items):
+    import torch
+
+    if torch.cuda.is_available():
+        return
+    skip = pytest.mark.skip(reason="no CUDA device")
+    for item in items:
+        if "gpu" in item.keywords:
+            item.add_marker(skip)

@@ -1,0 +1,209 @@
+"""Parity of the CUDA path (through the C ABI) with the CPU FP64 oracle.
+
+Bars (per component, relative L2 over the compared stations or cells):
+  FP64 spectral path vs the oracle            <= 1e-10
+  FP32 spectral path vs the oracle / FP64     <= 2e-5
+Components that vanish by symmetry (e.g. gxz on a one-column mesh) are
+compared against a floor of 1e-3 times the largest component norm of the
+same kind (gz alone, or the gradients), so rounding noise in the oracle does
+not count as a relative error.
+"""
+import numpy as np
+import pytest
+import torch
+
+from paper_2005_10160_gb300 import capi, workloads as W
+from paper_2005_10160_gb300.plan import Plan, kernel_values
+
+pytestmark = pytest.mark.gpu
+
+ALL7 = 0x7F
+TOL64 = 1e-10
+TOL32 = 2e-5
+
+
+def rel_errors(got, ref, comps):
+    """Relative L2 error per component with a symmetry floor."""
+    got = np.asarray(got, np.float64).reshape(len(ref), -1)
+    ref = np.asarray(ref, np.float64).reshape(len(ref), -1)
+    lst = capi.comp_list(comps)
+    norms = np.linalg.norm(ref, axis=1)
+    grad = [norms[i] for i, c in enumerate(lst) if c != 0]
+    gmax = max(grad) if grad else 0.0
+    out = []
+    for i, c in enumerate(lst):
+        floor = 1e-3 * (norms[i] if c == 0 else gmax)
+        den = max(norms[i], floor, 1e-300)
+        out.append(np.linalg.norm(got[i] - ref[i]) / den)
+    return np.array(out)
+
+
+def run_forward(mesh, comps, rho, fp64):
+    dt = torch.float64 if fp64 else torch.float32
+    with Plan(mesh, comps, fp64=fp64) as plan:
+        out = plan.forward(torch.as_tensor(np.asarray(rho), dtype=dt).cuda().contiguous())
+        torch.cuda.synchronize()
+        return out.cpu().numpy()
+
+
+def run_adjoint(mesh, comps, r, fp64):
+    dt = torch.float64 if fp64 else torch.float32
+    with Plan(mesh, comps, fp64=fp64) as plan:
+        out = plan.adjoint(torch.as_tensor(np.asarray(r), dtype=dt).cuda().contiguous())
+        torch.cuda.synchronize()
+        return out.cpu().numpy()
+
+
+SMALL_MESHES = [
+    (16, 16, 4, 10.0, 10.0, 10.0, 1.0),
+    (1, 1, 1, 5.0, 5.0, 5.0, 1.0),
+    (3, 5, 2, 10.0, 12.0, 8.0, 2.0),
+    (17, 9, 3, 25.0, 20.0, 10.0, 3.0),
+    (2, 33, 2, 10.0, 10.0, 10.0, 1.0),
+    (37, 29, 5, 20.0, 20.0, 15.0, 4.0),
+    (64, 1, 3, 10.0, 10.0, 10.0, 2.0),
+]
+
+
+@pytest.mark.parametrize("mesh", [(5, 4, 3, 10.0, 25.0, 20.0, 2.0), (9, 6, 2, 50.0, 50.0, 25.0, 10.0)])
+def test_kernel_values_match_oracle(gravlib, orc, mesh):
+    """FP64 kernel generation (Eq. 2 and the gradient forms over the offset
+    grid of Eq. 10) against the oracle's independent prism evaluation."""
+    nx, ny, nz, dx, dy, dz, h = mesh
+    K = kernel_values(mesh, ALL7).cpu().numpy()
+    for n in range(nz):
+        for v in range(-ny + 1, ny):
+            for u in range(-nx + 1, nx):
+                box = ((u - 0.5) * dx, (u + 0.5) * dx, (v - 0.5) * dy, (v + 0.5) * dy, n * dz, (n + 1) * dz)
+                ref = orc.prism((0.0, 0.0, -h), box)
+                got = K[:, n, v + ny - 1, u + nx - 1]
+                scale = np.abs(K[:, n]).reshape(7, -1).max(axis=1)
+                assert np.all(np.abs(got - ref) <= 1e-12 * np.abs(ref) + 1e-13 * scale), (n, u, v, got, ref)
+
+
+@pytest.mark.parametrize("mesh", SMALL_MESHES)
+def test_forward_fp64_matches_oracle(gravlib, orc, mesh):
+    nx, ny, nz = mesh[:3]
+    rng = np.random.default_rng(nx * 1000 + ny * 10 + nz)
+    rho = rng.uniform(-500, 500, (nz, ny, nx))
+    got = run_forward(mesh, ALL7, rho, fp64=True)
+    ref = orc.forward(mesh, ALL7, rho)
+    err = rel_errors(got, ref, ALL7)
+    assert np.all(err <= TOL64), err
+
+
+@pytest.mark.parametrize("mesh", SMALL_MESHES)
+def test_forward_fp32_matches_oracle(gravlib, orc, mesh):
+    nx, ny, nz = mesh[:3]
+    rng = np.random.default_rng(nx * 1000 + ny * 10 + nz + 1)
+    rho = rng.uniform(-500, 500, (nz, ny, nx)).astype(np.float32)
+    got = run_forward(mesh, ALL7, rho, fp64=False)
+    ref = orc.forward(mesh, ALL7, rho.astype(np.float64))
+    err = rel_errors(got, ref, ALL7)
+    assert np.all(err <= TOL32), err
+
+
+@pytest.mark.parametrize("mesh", SMALL_MESHES)
+@pytest.mark.parametrize("fp64", [True, False])
+def test_adjoint_matches_oracle(gravlib, orc, mesh, fp64):
+    nx, ny, nz = mesh[:3]
+    rng = np.random.default_rng(nx + 7 * ny + 31 * nz)
+    r = rng.normal(size=(7, ny, nx))
+    if not fp64:
+        r = r.astype(np.float32)
+    got = run_adjoint(mesh, ALL7, r, fp64)
+    ref = orc.adjoint(mesh, ALL7, np.asarray(r, np.float64))
+    err = np.linalg.norm(got - ref) / np.linalg.norm(ref)
+    assert err <= (TOL64 if fp64 else TOL32), err
+
+
+@pytest.mark.parametrize("comps", [capi.GRAV_GZ, capi.GRAV_GXZ, capi.GRAV_GYZ, capi.GRAV_GXY,
+                                   capi.GRAV_GZ | capi.GRAV_GZZ, capi.GRAV_ALL6, 0b1011010])
+def test_component_subsets(gravlib, orc, comps):
+    """Any component mask: output planes come in ascending bit order."""
+    mesh, rho = W.small16()
+    ref = orc.forward(mesh.tuple(), comps, rho)
+    got = run_forward(mesh.tuple(), comps, rho, fp64=True)
+    assert np.all(rel_errors(got, ref, comps) <= TOL64)
+    r = np.random.default_rng(comps).normal(size=ref.shape)
+    ga = run_adjoint(mesh.tuple(), comps, r, True)
+    gr = orc.adjoint(mesh.tuple(), comps, r)
+    assert np.linalg.norm(ga - gr) <= TOL64 * np.linalg.norm(gr)
+
+
+def test_paper_cube_model(gravlib, orc):
+    """Sec. 3.1: a 300 m cube 500-800 m deep (+300 kg/m^3) under 40x40
+    stations at 50 m spacing, 50 m up.  The fast forward agrees with the
+    exact single-prism field to about 13 orders of magnitude (Fig. 7)."""
+    mesh, rho, boxes = W.cube40()
+    got = run_forward(mesh.tuple(), ALL7, rho, fp64=True)
+    l0, l1, m0, m1, n0, n1, d = boxes[0]
+    ref = orc.box_field(mesh.tuple(), ALL7, (l0, l1, m0, m1, n0, n1), d).reshape(7, mesh.ny, mesh.nx)
+    err = rel_errors(got, ref, ALL7)
+    assert np.all(err <= 1e-12), err
+    got32 = run_forward(mesh.tuple(), ALL7, rho.astype(np.float32), fp64=False)
+    assert np.all(rel_errors(got32, ref, ALL7) <= TOL32)
+
+
+def test_boxes256_fp64_vs_oracle_and_superposition(gravlib, orc):
+    """256x256x32 mesh of 20 random boxes plus noise: sampled stations
+    against direct summation; the noise-free field against the sum of the
+    boxes' closed forms at every station."""
+    mesh, rho, boxes = W.boxes256()
+    comps = ALL7
+    got = run_forward(mesh.tuple(), comps, rho, fp64=True)
+    st = W.station_subset(mesh, 24, np.random.default_rng(5))
+    ref = orc.forward(mesh.tuple(), comps, rho, stations=st)
+    err = rel_errors(got.reshape(7, -1)[:, st], ref, comps)
+    assert np.all(err <= TOL64), err
+
+    _, rho_clean, _ = W.boxes256(noise=False)
+    got_clean = run_forward(mesh.tuple(), comps, rho_clean, fp64=True)
+    st2 = np.arange(0, mesh.nx * mesh.ny, 97, dtype=np.int64)
+    ref2 = sum(orc.box_field(mesh.tuple(), comps, b[:6], b[6], stations=st2) for b in boxes)
+    err2 = rel_errors(got_clean.reshape(7, -1)[:, st2], ref2, comps)
+    assert np.all(err2 <= TOL64), err2
+
+
+def test_dot_product_adjoint(gravlib):
+    """<G x, y> = <x, G^T y> on a ragged mesh, FP64 and FP32."""
+    mesh = (45, 23, 7, 20.0, 25.0, 10.0, 3.0)
+    rng = np.random.default_rng(11)
+    x = rng.normal(size=(7, 23, 45))
+    y = rng.normal(size=(7, 23, 45))
+    for fp64, tol in ((True, 1e-12), (False, 1e-5)):
+        dt = torch.float64 if fp64 else torch.float32
+        with Plan(mesh, ALL7, fp64=fp64) as plan:
+            xt = torch.as_tensor(x, dtype=dt).cuda()
+            yt = torch.as_tensor(y, dtype=dt).cuda()
+            gx = plan.forward(xt).double()
+            gty = plan.adjoint(yt).double()
+            lhs = float((gx * yt.double()).sum())
+            rhs = float((xt.double() * gty).sum())
+        assert abs(lhs - rhs) <= tol * max(abs(lhs), abs(rhs)), (fp64, lhs, rhs)
+
+
+def test_repeatable_and_stream_ordered(gravlib):
+    """Two calls give bit-identical results, on a non-default stream too."""
+    mesh, rho = W.small16()
+    with Plan(mesh, ALL7) as plan:
+        x = torch.as_tensor(rho, dtype=torch.float32).cuda()
+        a = plan.forward(x).clone()
+        s = torch.cuda.Stream()
+        s.wait_stream(torch.cuda.current_stream())
+        with torch.cuda.stream(s):
+            b = plan.forward(x, stream=s)
+        torch.cuda.synchronize()
+        assert torch.equal(a, b)
+
+
+def test_max_size_axes(gravlib, orc):
+    """Largest axes the plan accepts (nx = 2048 with ny small, ny = 1024 with
+    nx small), against the oracle at a few stations."""
+    for mesh in [(capi.GRAV_MAX_NX, 2, 1, 10.0, 10.0, 10.0, 5.0), (3, capi.GRAV_MAX_NY, 1, 10.0, 10.0, 10.0, 5.0)]:
+        nx, ny, nz = mesh[:3]
+        rho = np.random.default_rng(nx + ny).uniform(-300, 300, (nz, ny, nx))
+        got = run_forward(mesh, ALL7, rho, fp64=True)
+        st = np.array([0, nx * ny - 1, (ny // 2) * nx + nx // 2, 1, nx * ny // 3], dtype=np.int32)
+        ref = orc.forward(mesh, ALL7, rho, stations=st)
+        assert np.all(rel_errors(got.reshape(7, -1)[:, st], ref, ALL7) <= TOL64)
