@@ -1,0 +1,438 @@
+#!/usr/bin/env python
+"""Throughput of the fast gravity / gravity-gradient forward on GB300.
+
+One step = one forward of all six components (gz, gxx, gxy, gxz, gyy, gyz)
+through the C ABI: row transforms of the density, the fused column stage
+(column FFTs, product with the resident FP32 kernel spectra, compensated
+layer sum, inverse column FFTs) and inverse row transforms (Eq. 21).
+
+Workload: 1024 x 1024 x 100 cells of 50 x 50 x 25 m, stations 10 m above
+the top, density a seeded smooth Gaussian random field (std 200 kg/m^3,
+correlation length 20 cells) in float32.  Metric: cell-station pairs per
+second, (nx ny) * (nx ny nz) = 1.0995e14 pairs per forward.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Multi-GPU (torchrun, one rank per GPU): every rank runs its own replica of
+the workload (the forward needs no exchange between ranks); value is the
+pairs of all ranks over the slowest rank's time (weak scaling).
+
+``--impl reference`` times the CPU FP64 direct-summation oracle on the
+host cores instead, on a bounded sample of the same workload per step.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+WORKLOADS = {
+    # name: (nx, ny, nz, dx, dy, dz, h)
+    "grf1024": (1024, 1024, 100, 50.0, 50.0, 25.0, 10.0),
+    "boxes512": (512, 512, 64, 20.0, 20.0, 20.0, 10.0),
+    "boxes256": (256, 256, 32, 25.0, 25.0, 20.0, 5.0),
+}
+METRIC = "6-comp forward cell·station pairs/s at 1024²×100, %HBM roofline; serve p50/p99"
+COMPS = 63
+NCOMP = 6
+FALLBACK_HBM_GBS = 6800.0
+PROFILE_SUMMARY = os.path.join(ROOT, "profiles", "forward_columns_grf1024.md")
+KERNEL_SOURCES = ("fft_block.cuh", "spectral.cuh", "spectral_launch.cuh", "col_fwd_f32.cu", "grav_internal.h")
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", choices=("ours", "reference"), default="ours")
+    ap.add_argument("--workload", choices=tuple(WORKLOADS), default="grf1024")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-fp64", action="store_true", help="skip the FP64-spectral comparison leg")
+    return ap.parse_args()
+
+
+def pairs_per_forward(mesh):
+    nx, ny, nz = mesh[:3]
+    return float(nx * ny) * float(nx * ny * nz)
+
+
+def kernel_digest() -> str:
+    h = hashlib.sha256()
+    for f in KERNEL_SOURCES:
+        with open(os.path.join(ROOT, "paper_2005_10160_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def profiled_traffic(digest: str):
+    """DRAM bytes per column-stage launch from the committed ncu summary, or
+    None when the summary is missing or the kernel changed since."""
+    try:
+        text = open(PROFILE_SUMMARY).read()
+    except OSError:
+        return None
+    vals = {}
+    for line in text.splitlines():
+        if ":" in line and line.strip().startswith("- "):
+            k, v = line.strip()[2:].split(":", 1)
+            vals[k.strip()] = v.strip().strip("`")
+    if vals.get("kernel_digest") != digest:
+        return None
+    try:
+        return float(vals["dram_bytes_per_launch_full_size"])
+    except (KeyError, ValueError):
+        return None
+
+
+def hbm_peak():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as fh:
+            d = json.load(fh)
+        return float(d["hbm_gbs"]), "measured"
+    except (OSError, KeyError, ValueError):
+        return FALLBACK_HBM_GBS, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons every 100 ms in the background."""
+
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_id: str):
+        self.gpu_id = gpu_id
+        self.proc = None
+        self.lines = []
+        self.thread = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", self.gpu_id, f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "100"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+            return
+        self.thread = threading.Thread(target=self._read, daemon=True)
+        self.thread.start()
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append((time.time(), line.strip()))
+
+    def stop(self):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+        if self.thread:
+            self.thread.join(timeout=5)
+
+    def summary(self, t0, t1):
+        rows = []
+        for t, line in self.lines:
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 8:
+                continue
+            try:
+                rows.append((t, float(parts[0]), float(parts[1]), parts[4:8]))
+            except ValueError:
+                continue
+        window = [r for r in rows if t0 <= r[0] <= t1]
+        label = "timed"
+        if not window:
+            window, label = rows, "warmup+timed"
+        if not window:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"], "samples": 0}
+        names = ("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap")
+        reasons = sorted({names[i] for r in window for i, v in enumerate(r[3]) if v.lower() == "active"})
+        return {"sm_mhz": statistics.median(r[1] for r in window), "sm_max_mhz": max(r[2] for r in window),
+                "reasons": reasons, "samples": len(window), "window": label}
+
+
+def dist_setup(n_gpus):
+    import torch
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        import torch.distributed as dist
+
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    elif torch.cuda.is_available():
+        torch.cuda.set_device(0)
+    return world, rank, local
+
+
+def barrier(world):
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.barrier()
+
+
+def max_over_ranks(world, value: float) -> float:
+    if world == 1:
+        return value
+    import torch
+    import torch.distributed as dist
+
+    t = torch.tensor([value], dtype=torch.float64, device="cuda")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def oracle_rate(mesh, rho_np, n_stations, n_layers, threads):
+    """Pairs/s of the CPU oracle on n_stations stations x the top n_layers."""
+    import numpy as np
+
+    import oracle
+    from paper_2005_10160_gb300 import workloads
+
+    nx, ny, nz, dx, dy, dz, h = mesh
+    sub = (nx, ny, n_layers, dx, dy, dz, h)
+    st = workloads.station_subset(workloads.Mesh(*sub), n_stations, np.random.default_rng(7))
+    rho = np.ascontiguousarray(rho_np[:n_layers], dtype=np.float64)
+    t0 = time.perf_counter()
+    oracle.forward(sub, COMPS, rho, stations=st, nthreads=threads)
+    dt = time.perf_counter() - t0
+    pairs = float(len(st)) * nx * ny * n_layers
+    return pairs / dt, pairs, dt
+
+
+def cpu_density_sample(mesh, n_layers):
+    """The leading layers of the workload's density on the CPU (float32)."""
+    import torch
+
+    from paper_2005_10160_gb300 import workloads
+
+    nx, ny, nz = mesh[:3]
+    _, rho = workloads.grf1024(nx, ny, nz, device="cuda" if torch.cuda.is_available() else "cpu")
+    return rho[:n_layers].float().cpu().numpy()
+
+
+def run_reference(args):
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return 0
+    import oracle
+
+    oracle.build()
+    mesh = WORKLOADS[args.workload]
+    cores = os.cpu_count() or 1
+    rho = cpu_density_sample(mesh, mesh[2])
+    # calibrate, then size each step to keep the whole run within ~2.5 minutes
+    rate0, _, _ = oracle_rate(mesh, rho, cores, 1, cores)
+    per_step_s = 150.0 / max(1, args.steps + args.warmup)
+    layers = int(max(1, min(mesh[2], per_step_s * rate0 / (cores * mesh[0] * mesh[1]))))
+    for _ in range(args.warmup):
+        oracle_rate(mesh, rho, cores, layers, cores)
+    tot_pairs = tot_s = 0.0
+    for _ in range(args.steps):
+        _, p, dt = oracle_rate(mesh, rho, cores, layers, cores)
+        tot_pairs += p
+        tot_s += dt
+    value = tot_pairs / tot_s
+    sample = f"{cores} stations x top {layers} of {mesh[2]} layers x {mesh[0]}x{mesh[1]} cells per step"
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": "pairs/s", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000.0 * tot_s / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": f"{args.workload} {mesh[0]}x{mesh[1]}x{mesh[2]}, {NCOMP} components",
+                   "sample": sample},
+        "cpu_baseline": {"value": value, "unit": "pairs/s", "cores": cores, "kind": "oracle", "sample": sample},
+        "e2e": {"value": value, "unit": "pairs/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def run_ours(args):
+    import numpy as np
+    import torch
+
+    from paper_2005_10160_gb300 import build as gbuild
+    from paper_2005_10160_gb300 import capi, workloads
+    from paper_2005_10160_gb300.plan import Plan
+
+    world, rank, local = dist_setup(args.gpus)
+    if rank == 0:
+        gbuild.build()
+    barrier(world)
+    capi.lib()
+    dev = torch.device("cuda", torch.cuda.current_device())
+    mesh = WORKLOADS[args.workload]
+    nx, ny, nz = mesh[:3]
+    pairs = pairs_per_forward(mesh)
+
+    if args.workload == "grf1024":
+        _, rho = workloads.grf1024(nx, ny, nz, device=dev)
+    else:
+        m = workloads.Mesh(*mesh)
+        rho = torch.as_tensor(workloads.serving_density(m, workloads.rng_for(9)), device=dev)
+    rho = rho.to(torch.float32).contiguous()
+
+    t0 = time.perf_counter()
+    plan = Plan(mesh, COMPS, fp64=False)
+    torch.cuda.synchronize()
+    plan_s = time.perf_counter() - t0
+    out = torch.empty((NCOMP, ny, nx), dtype=torch.float32, device=dev)
+    stream = torch.cuda.current_stream(dev)
+
+    props = torch.cuda.get_device_properties(dev)
+    gpu_id = str(getattr(props, "uuid", local))
+    if gpu_id and not gpu_id.startswith("GPU-") and len(gpu_id) > 8:
+        gpu_id = "GPU-" + gpu_id
+    sampler = ClockSampler(gpu_id)
+    sampler.start()
+
+    for _ in range(args.warmup):
+        plan.forward(rho, out)
+    torch.cuda.synchronize()
+    capi.grav_plan_set_timing(plan.handle, True)
+    capi.grav_plan_stage_times(plan.handle)  # reset
+
+    barrier(world)
+    torch.cuda.synchronize()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    t_wall0 = time.time()
+    ev0.record(stream)
+    for _ in range(args.steps):
+        plan.forward(rho, out)
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    t_wall1 = time.time()
+    barrier(world)
+    ms = ev0.elapsed_time(ev1)
+    stage_ms, n_fwd, _ = capi.grav_plan_stage_times(plan.handle)
+    capi.grav_plan_set_timing(plan.handle, False)
+    ms_max = max_over_ranks(world, ms)
+    sampler.stop()
+    clocks = sampler.summary(t_wall0 - 0.05, t_wall1 + 0.05)
+
+    ms_per_step = ms_max / args.steps
+    value = world * pairs * args.steps / (ms_max / 1000.0)
+
+    # roofline of the dominant kernel: the column stage
+    kx = plan.px // 2 + 1
+    hy = plan.py // 2 + 1
+    spec_b = NCOMP * nz * kx * hy * 4
+    x_b = kx * nz * ny * 8
+    y_b = 2 * kx * NCOMP * ny * 8
+    col_alg = spec_b + x_b + y_b
+    col_ms = stage_ms["forward_columns"] / max(1, n_fwd)
+    peak, peak_kind = hbm_peak()
+    achieved = col_alg / (col_ms / 1000.0) / 1e9
+    digest = kernel_digest()
+    traffic = profiled_traffic(digest)
+    roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+                "traffic": traffic, "kernel": "forward_column_kernel (column stage)",
+                "algorithmic_bytes": col_alg, "avg_launch_ms": col_ms, "peak_kind": peak_kind,
+                "stage_ms": {k: v / max(1, n_fwd) for k, v in stage_ms.items() if k.startswith("forward")}}
+    fwd_alg = spec_b + 4 * nx * ny * nz + 4 * NCOMP * nx * ny
+
+    # end to end through the public API with pinned host buffers
+    rho_h = rho.cpu().pin_memory()
+    out_h = torch.empty((NCOMP, ny, nx), dtype=torch.float32).pin_memory()
+    rho_d = torch.empty_like(rho)
+    for _ in range(max(1, args.warmup)):
+        rho_d.copy_(rho_h, non_blocking=True)
+        plan.forward(rho_d, out)
+        out_h.copy_(out, non_blocking=True)
+    torch.cuda.synchronize()
+    e_steps = max(3, min(args.steps, 50))
+    barrier(world)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(e_steps):
+        rho_d.copy_(rho_h, non_blocking=True)
+        plan.forward(rho_d, out)
+        out_h.copy_(out, non_blocking=True)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    barrier(world)
+    e_ms = max_over_ranks(world, e0.elapsed_time(e1))
+    e2e = {"value": world * pairs * e_steps / (e_ms / 1000.0), "unit": "pairs/s",
+           "h2d_bytes_per_step": rho_h.numel() * 4, "d2h_bytes_per_step": out_h.numel() * 4,
+           "steps": e_steps, "ms_per_step": e_ms / e_steps}
+
+    # the all-FP64 spectral path on the same workload, for context
+    fp64 = None
+    if not args.no_fp64 and rank == 0:
+        plan64 = Plan(mesh, COMPS, fp64=True)
+        rho64 = rho.double()
+        out64 = torch.empty((NCOMP, ny, nx), dtype=torch.float64, device=dev)
+        plan64.forward(rho64, out64)
+        torch.cuda.synchronize()
+        f0, f1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        f0.record(stream)
+        n64 = 3
+        for _ in range(n64):
+            plan64.forward(rho64, out64)
+        f1.record(stream)
+        torch.cuda.synchronize()
+        ms64 = f0.elapsed_time(f1) / n64
+        rel = (torch.linalg.vector_norm((out.double() - out64).reshape(NCOMP, -1), dim=1)
+               / torch.linalg.vector_norm(out64.reshape(NCOMP, -1), dim=1)).cpu().tolist()
+        fp64 = {"ms_per_step": ms64, "value": pairs / (ms64 / 1000.0),
+                "fp32_vs_fp64_rel_l2": rel}
+        plan64.close()
+        del rho64, out64
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline and args.workload == "grf1024":
+        cores = os.cpu_count() or 1
+        layers = 16
+        rho_np = rho[:layers].cpu().numpy()
+        rate, p, dt = oracle_rate(mesh, rho_np, cores, layers, cores)
+        cpu = {"value": rate, "unit": "pairs/s", "cores": cores, "kind": "oracle",
+               "sample": f"{cores} stations x top {layers} layers x {nx}x{ny} cells ({p:.3g} pairs, {dt:.1f} s)"}
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": "pairs/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": f"{args.workload} {nx}x{ny}x{nz} cells {mesh[3]:g}x{mesh[4]:g}x{mesh[5]:g} m, "
+                                   f"h={mesh[6]:g} m, {NCOMP} components, FP32 spectra",
+                       "pairs_per_step": pairs, "l2": "inputs larger than L2 (spectra %.2f GB)" % (spec_b / 1e9),
+                       "parallelism": f"replica x{world}", "plan_create_s": plan_s,
+                       "forward_algorithmic_bytes": fwd_alg},
+            "roofline": roofline, "clocks": clocks, "e2e": e2e, "gpu_launches": 3 * args.steps,
+            "cpu_baseline": cpu, "fp64_path": fp64,
+        }
+        print(json.dumps(line), flush=True)
+    plan.close()
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.destroy_process_group()
+    return 0
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -141,6 +141,22 @@ int grav_plan_info(const grav_plan* plan, grav_plan_info_t* info);
 int grav_kernel_values(int nx, int ny, int nz, double dx, double dy, double dz, double h,
                        unsigned components, double* K_dev, void* stream);
 
+/* Stage timing, for tracing and roofline measurement.  While enabled, every
+ * grav_forward / grav_adjoint records CUDA events on its stream before and
+ * after each of its three stages (row transforms, column stage, inverse row
+ * transforms).  Enabling adds four event records per call and no
+ * synchronisation.  Returns GRAV_OK, GRAV_EINVAL or GRAV_ECUDA. */
+int grav_plan_set_timing(grav_plan* plan, int enable);
+
+/* Waits for the recorded events, adds up the device time of each stage since
+ * the previous read, and resets the record.
+ *   ms[0..2]  forward: row transforms, column stage, inverse row transforms
+ *   ms[3..5]  adjoint: the same three stages
+ *   calls[0]  forward calls timed, calls[1] adjoint calls timed
+ * At most 65536 calls are kept between reads; later calls are not timed.
+ * Returns GRAV_OK, GRAV_EINVAL or GRAV_ECUDA. */
+int grav_plan_stage_times(grav_plan* plan, double ms[6], long long calls[2]);
+
 #ifdef __cplusplus
 }
 #endif

@@ -31,6 +31,8 @@ EXPORTED = (
     "grav_plan_bytes",
     "grav_plan_info",
     "grav_kernel_values",
+    "grav_plan_set_timing",
+    "grav_plan_stage_times",
 )
 
 
@@ -80,6 +82,10 @@ def lib() -> ctypes.CDLL:
             L.grav_plan_info.restype = i
             L.grav_kernel_values.argtypes = [i, i, i, d, d, d, d, u, p, p]
             L.grav_kernel_values.restype = i
+            L.grav_plan_set_timing.argtypes = [p, i]
+            L.grav_plan_set_timing.restype = i
+            L.grav_plan_stage_times.argtypes = [p, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_longlong)]
+            L.grav_plan_stage_times.restype = i
             _lib = L
     return _lib
 
@@ -135,3 +141,19 @@ def grav_kernel_values(nx, ny, nz, dx, dy, dz, h, components, K_ptr, stream=0) -
 
 def comp_list(components: int) -> list[int]:
     return [c for c in range(7) if components & (1 << c)]
+
+
+def grav_plan_set_timing(plan, enable: bool) -> int:
+    return _check(lib().grav_plan_set_timing(plan, 1 if enable else 0))
+
+
+STAGES = ("forward_rows", "forward_columns", "forward_inverse_rows",
+          "adjoint_rows", "adjoint_columns", "adjoint_inverse_rows")
+
+
+def grav_plan_stage_times(plan):
+    """(ms per stage as a dict, forward calls, adjoint calls) since the last read."""
+    ms = (ctypes.c_double * 6)()
+    calls = (ctypes.c_longlong * 2)()
+    _check(lib().grav_plan_stage_times(plan, ms, calls))
+    return dict(zip(STAGES, list(ms))), int(calls[0]), int(calls[1])

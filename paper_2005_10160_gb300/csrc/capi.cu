@@ -105,6 +105,9 @@ int dev_alloc(T** p, size_t bytes, const char* what) {
 
 void free_plan(grav_plan* p) {
     if (!p) return;
+    for (auto& t : p->timed)
+        for (cudaEvent_t e : t.ev) p->ev_pool.push_back(e);
+    for (cudaEvent_t e : p->ev_pool) cudaEventDestroy(e);
     cudaFree(p->spec);
     cudaFree(p->tw);
     cudaFree(p->ws_a);
@@ -210,37 +213,72 @@ int make_spectra(grav_plan* p) {
     return rc;
 }
 
+constexpr size_t kMaxTimedCalls = 65536;
+
+// Events of one timed call, or nullptr when timing is off or full.
+grav_plan::TimedCall* begin_timed(grav_plan* p, int kind) {
+    if (!p->timing || p->timed.size() >= kMaxTimedCalls) return nullptr;
+    grav_plan::TimedCall t;
+    t.kind = kind;
+    for (int i = 0; i < 4; ++i) {
+        if (!p->ev_pool.empty()) {
+            t.ev[i] = p->ev_pool.back();
+            p->ev_pool.pop_back();
+        } else if (cudaEventCreate(&t.ev[i]) != cudaSuccess) {
+            cudaGetLastError();
+            for (int j = 0; j < i; ++j) p->ev_pool.push_back(t.ev[j]);
+            return nullptr;
+        }
+    }
+    p->timed.push_back(t);
+    return &p->timed.back();
+}
+
+inline void mark(grav_plan::TimedCall* t, int i, cudaStream_t s) {
+    if (t) cudaEventRecord(t->ev[i], s);
+}
+
 template <typename R>
 int run_forward(grav_plan* p, const void* rho, void* out, cudaStream_t s) {
     cudaError_t e;
+    grav_plan::TimedCall* tc = begin_timed(p, 0);
+    mark(tc, 0, s);
     e = launch_row_r2c<R>(p->log_px, (const R*)rho, (size_t)p->ny * p->nx, (size_t)p->nx, p->nx, p->ny, p->nz, p->ws_a,
                           p->ny_pad, p->tw, p->log_t, s);
     if (e != cudaSuccess) return cuda_fail(e, "forward row transform");
+    mark(tc, 1, s);
     ColumnArgs a{p->ny, p->ny_pad, p->nz, p->ncomp, p->kx_count, p->jp, p->imag_mask, p->oddv_mask,
                  p->log_t - (p->log_py - 1), p->log_t - p->log_py};
     e = launch_forward_columns<R>(p->log_py - 1, a, p->ws_a, (const R*)p->spec, p->ws_b, p->tw, s);
     if (e != cudaSuccess) return cuda_fail(e, "forward column stage");
+    mark(tc, 2, s);
     const size_t half = (size_t)p->kx_count * p->ncomp * p->ny_pad * 2 * sizeof(R);
     e = launch_row_c2r<R>(p->log_px, p->ws_b, (const unsigned char*)p->ws_b + half, p->ny, p->ncomp, p->ny_pad, (R*)out,
                           (size_t)p->nx, p->nx, p->tw, p->log_t, s);
     if (e != cudaSuccess) return cuda_fail(e, "forward inverse row transform");
+    mark(tc, 3, s);
     return GRAV_OK;
 }
 
 template <typename R>
 int run_adjoint(grav_plan* p, const void* r, void* grad, cudaStream_t s) {
     cudaError_t e;
+    grav_plan::TimedCall* tc = begin_timed(p, 1);
+    mark(tc, 0, s);
     e = launch_row_r2c<R>(p->log_px, (const R*)r, (size_t)p->ny * p->nx, (size_t)p->nx, p->nx, p->ny, p->ncomp,
                           p->ws_b, p->ny_pad, p->tw, p->log_t, s);
     if (e != cudaSuccess) return cuda_fail(e, "adjoint row transform");
+    mark(tc, 1, s);
     ColumnArgs a{p->ny, p->ny_pad, p->nz, p->ncomp, p->kx_count, p->jp, p->imag_mask, p->oddv_mask,
                  p->log_t - (p->log_py - 1), p->log_t - p->log_py};
     e = launch_adjoint_columns<R>(p->log_py - 1, a, p->ws_b, (const R*)p->spec, p->ws_a, p->tw, s);
     if (e != cudaSuccess) return cuda_fail(e, "adjoint column stage");
+    mark(tc, 2, s);
     const size_t half = (size_t)p->kx_count * p->nz * p->ny_pad * 2 * sizeof(R);
     e = launch_row_c2r<R>(p->log_px, p->ws_a, (const unsigned char*)p->ws_a + half, p->ny, p->nz, p->ny_pad, (R*)grad,
                           (size_t)p->nx, p->nx, p->tw, p->log_t, s);
     if (e != cudaSuccess) return cuda_fail(e, "adjoint inverse row transform");
+    mark(tc, 3, s);
     return GRAV_OK;
 }
 
@@ -269,12 +307,11 @@ const char* grav_last_error(void) { return g_err; }
 grav_plan* grav_plan_create(int nx, int ny, int nz, double dx, double dy, double dz, double h, unsigned components) {
     g_err[0] = 0;
     if (check_geometry(nx, ny, nz, dx, dy, dz, h, components)) return nullptr;
-    grav_plan* p = new (std::nothrow) grav_plan;
+    grav_plan* p = new (std::nothrow) grav_plan();
     if (!p) {
         set_error("host allocation of the plan failed");
         return nullptr;
     }
-    memset(p, 0, sizeof *p);
     p->nx = nx; p->ny = ny; p->nz = nz;
     p->dx = dx; p->dy = dy; p->dz = dz; p->h = h;
     p->comps = components & 0x7Fu;
@@ -383,6 +420,37 @@ int grav_kernel_values(int nx, int ny, int nz, double dx, double dy, double dz, 
     cudaError_t e = launch_kernel_gen(g, components & 0x7Fu, 0, nz, 1, 0, 0, K_dev, (cudaStream_t)stream);
     if (e != cudaSuccess) return cuda_fail(e, "kernel generation launch");
     return GRAV_OK;
+}
+
+int grav_plan_set_timing(grav_plan* plan, int enable) {
+    if (!plan) {
+        set_error("grav_plan_set_timing: null plan");
+        return GRAV_EINVAL;
+    }
+    plan->timing = enable ? 1 : 0;
+    return GRAV_OK;
+}
+
+int grav_plan_stage_times(grav_plan* plan, double ms[6], long long calls[2]) {
+    if (!plan || !ms || !calls) {
+        set_error("grav_plan_stage_times: null argument");
+        return GRAV_EINVAL;
+    }
+    for (int i = 0; i < 6; ++i) ms[i] = 0.0;
+    calls[0] = calls[1] = 0;
+    int rc = GRAV_OK;
+    for (auto& t : plan->timed) {
+        cudaError_t e = cudaEventSynchronize(t.ev[3]);
+        if (e != cudaSuccess && rc == GRAV_OK) rc = cuda_fail(e, "cudaEventSynchronize(stage timing)");
+        for (int i = 0; i < 3 && e == cudaSuccess; ++i) {
+            float v = 0.f;
+            if (cudaEventElapsedTime(&v, t.ev[i], t.ev[i + 1]) == cudaSuccess) ms[3 * t.kind + i] += v;
+        }
+        calls[t.kind] += 1;
+        for (cudaEvent_t ev : t.ev) plan->ev_pool.push_back(ev);
+    }
+    plan->timed.clear();
+    return rc;
 }
 
 }  // extern "C"

@@ -4,6 +4,8 @@
 #include <stddef.h>
 #include <stdint.h>
 
+#include <vector>
+
 #include "../../include/grav.h"
 
 namespace grav {
@@ -68,6 +70,14 @@ struct grav_plan {
     void* ws_b;     // workspace: forward column outputs / adjoint row transforms
     size_t spec_bytes, tw_bytes, ws_a_bytes, ws_b_bytes;
     int device;
+    // stage timing (grav_plan_set_timing)
+    int timing;
+    std::vector<cudaEvent_t> ev_pool;
+    struct TimedCall {
+        int kind;  // 0 forward, 1 adjoint
+        cudaEvent_t ev[4];
+    };
+    std::vector<TimedCall> timed;
 };
 
 namespace grav {
