@@ -157,6 +157,35 @@ int grav_plan_set_timing(grav_plan* plan, int enable);
  * Returns GRAV_OK, GRAV_EINVAL or GRAV_ECUDA. */
 int grav_plan_stage_times(grav_plan* plan, double ms[6], long long calls[2]);
 
+/* Size of the library's static device scratch area (16 MiB per GPU). */
+#define GRAV_STATIC_SCRATCH_BYTES (16u << 20)
+
+/* Forward for callers that cannot allocate device memory.  The paper has no
+ * counterpart: this is a library convenience.
+ *
+ * A caller whose device memory is all reserved by another framework's
+ * allocator, or a serving loop that must not call cudaMalloc (it can
+ * synchronise the device), creates its plans at start-up and may then need
+ * scratch for a forward without asking for memory, for instance to run a
+ * second forward on the same plan on another stream.  This entry point
+ * computes exactly what grav_forward computes, with the same arguments,
+ * types and status codes, but takes its per-call scratch from one static
+ * array of GRAV_STATIC_SCRATCH_BYTES that the library holds on every GPU it
+ * is loaded on, instead of the plan's workspaces.  It allocates nothing.
+ *
+ * Limits and rules:
+ *   - the plan's scratch need, (px/2 + 1) ny' (nz + 2 ncomp) complex values
+ *     (ny' = ny rounded up to a multiple of 4, FP32 or FP64 as the plan),
+ *     must fit in GRAV_STATIC_SCRATCH_BYTES; otherwise GRAV_EINVAL with the
+ *     sizes in grav_last_error().  FP32 meshes up to 128 x 128 x 32 fit.
+ *   - the current device must be the plan's device (GRAV_EINVAL otherwise).
+ *   - the first call on a device looks up the array's device address with
+ *     that device current; make that first call before any stream capture.
+ *   - every call, on any plan, shares the one array: calls whose work
+ *     overlaps on the GPU race and give wrong results.  Order them on one
+ *     stream or with events.  No contents need clearing between calls. */
+int grav_forward_static_scratch(grav_plan* plan, const void* rho_dev, void* out_dev, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

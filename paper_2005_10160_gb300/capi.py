@@ -17,6 +17,7 @@ GRAV_ALL6 = 63
 GRAV_FP64_SPECTRAL = 1 << 16
 GRAV_OK, GRAV_EINVAL, GRAV_ENOMEM, GRAV_ECUDA, GRAV_ETIMEOUT = 0, -1, -2, -3, -4
 GRAV_MAX_NX, GRAV_MAX_NY = 2048, 1024
+GRAV_STATIC_SCRATCH_BYTES = 16 << 20
 
 COMPONENT_NAMES = ("gz", "gxx", "gxy", "gxz", "gyy", "gyz", "gzz")
 
@@ -33,6 +34,7 @@ EXPORTED = (
     "grav_kernel_values",
     "grav_plan_set_timing",
     "grav_plan_stage_times",
+    "grav_forward_static_scratch",
 )
 
 
@@ -86,6 +88,8 @@ def lib() -> ctypes.CDLL:
             L.grav_plan_set_timing.restype = i
             L.grav_plan_stage_times.argtypes = [p, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_longlong)]
             L.grav_plan_stage_times.restype = i
+            L.grav_forward_static_scratch.argtypes = [p, p, p, p]
+            L.grav_forward_static_scratch.restype = i
             _lib = L
     return _lib
 
@@ -157,3 +161,9 @@ def grav_plan_stage_times(plan):
     calls = (ctypes.c_longlong * 2)()
     _check(lib().grav_plan_stage_times(plan, ms, calls))
     return dict(zip(STAGES, list(ms))), int(calls[0]), int(calls[1])
+
+
+def grav_forward_static_scratch(plan, rho_ptr, out_ptr, stream=0) -> int:
+    """grav_forward without the plan's workspaces: scratch comes from the
+    library's static device array (for callers that cannot allocate)."""
+    return _check(lib().grav_forward_static_scratch(plan, rho_ptr, out_ptr, stream or None))
