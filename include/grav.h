@@ -157,6 +157,20 @@ int grav_plan_set_timing(grav_plan* plan, int enable);
  * Returns GRAV_OK, GRAV_EINVAL or GRAV_ECUDA. */
 int grav_plan_stage_times(grav_plan* plan, double ms[6], long long calls[2]);
 
+/* Waits for the device, then reports whether a bounded wait inside an
+ * earlier call on this plan ran out (the column stage streams its inputs
+ * through asynchronous copies and gives up after one second instead of
+ * hanging).  Returns GRAV_OK, GRAV_ETIMEOUT (that call's output is invalid;
+ * the flag is cleared) or GRAV_ECUDA. */
+int grav_plan_check(grav_plan* plan);
+
+/* Failure-path self-test: one GPU thread waits, with the same bounded wait
+ * the pipelines use, on a barrier that nothing completes, for limit_ms
+ * milliseconds (0 < limit_ms <= 10000).  Expected result: GRAV_ETIMEOUT, with
+ * the time actually waited in *waited_ms (may be NULL); the CUDA context
+ * stays usable.  GRAV_OK would mean the wait did not run out. */
+int grav_selftest_bounded_wait(double limit_ms, double* waited_ms);
+
 /* Size of the library's static device scratch area (16 MiB per GPU). */
 #define GRAV_STATIC_SCRATCH_BYTES (16u << 20)
 

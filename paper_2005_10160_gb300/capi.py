@@ -35,6 +35,8 @@ EXPORTED = (
     "grav_plan_set_timing",
     "grav_plan_stage_times",
     "grav_forward_static_scratch",
+    "grav_plan_check",
+    "grav_selftest_bounded_wait",
 )
 
 
@@ -90,6 +92,10 @@ def lib() -> ctypes.CDLL:
             L.grav_plan_stage_times.restype = i
             L.grav_forward_static_scratch.argtypes = [p, p, p, p]
             L.grav_forward_static_scratch.restype = i
+            L.grav_plan_check.argtypes = [p]
+            L.grav_plan_check.restype = i
+            L.grav_selftest_bounded_wait.argtypes = [d, ctypes.POINTER(ctypes.c_double)]
+            L.grav_selftest_bounded_wait.restype = i
             _lib = L
     return _lib
 
@@ -167,3 +173,15 @@ def grav_forward_static_scratch(plan, rho_ptr, out_ptr, stream=0) -> int:
     """grav_forward without the plan's workspaces: scratch comes from the
     library's static device array (for callers that cannot allocate)."""
     return _check(lib().grav_forward_static_scratch(plan, rho_ptr, out_ptr, stream or None))
+
+
+def grav_plan_check(plan) -> int:
+    """Raises GravError(GRAV_ETIMEOUT) if a bounded wait of an earlier call ran out."""
+    return _check(lib().grav_plan_check(plan))
+
+
+def grav_selftest_bounded_wait(limit_ms: float):
+    """(status code, milliseconds waited) of the bounded-wait self-test."""
+    waited = ctypes.c_double(0.0)
+    rc = lib().grav_selftest_bounded_wait(float(limit_ms), ctypes.byref(waited))
+    return rc, waited.value

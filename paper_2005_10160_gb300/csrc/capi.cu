@@ -112,6 +112,7 @@ void free_plan(grav_plan* p) {
     cudaFree(p->tw);
     cudaFree(p->ws_a);
     cudaFree(p->ws_b);
+    cudaFree(p->err_flag);
     delete p;
 }
 
@@ -249,7 +250,7 @@ int run_forward(grav_plan* p, const void* rho, void* out, cudaStream_t s) {
     mark(tc, 1, s);
     ColumnArgs a{p->ny, p->ny_pad, p->nz, p->ncomp, p->kx_count, p->jp, p->imag_mask, p->oddv_mask,
                  p->log_t - (p->log_py - 1), p->log_t - p->log_py};
-    e = launch_forward_columns<R>(p->log_py - 1, a, p->ws_a, (const R*)p->spec, p->ws_b, p->tw, s);
+    e = launch_forward_columns<R>(p->log_py - 1, a, p->ws_a, (const R*)p->spec, p->ws_b, p->tw, p->err_flag, s);
     if (e != cudaSuccess) return cuda_fail(e, "forward column stage");
     mark(tc, 2, s);
     const size_t half = (size_t)p->kx_count * p->ncomp * p->ny_pad * 2 * sizeof(R);
@@ -357,6 +358,11 @@ grav_plan* grav_plan_create(int nx, int ny, int nz, double dx, double dy, double
     if (!rc) rc = dev_alloc(&p->spec, p->spec_bytes, "kernel spectra");
     if (!rc) rc = dev_alloc(&p->ws_a, p->ws_a_bytes, "workspace A");
     if (!rc) rc = dev_alloc(&p->ws_b, p->ws_b_bytes, "workspace B");
+    if (!rc) rc = dev_alloc(&p->err_flag, 256, "error flag");
+    if (!rc) {
+        cudaError_t me = cudaMemset(p->err_flag, 0, 256);
+        if (me != cudaSuccess) rc = cuda_fail(me, "cudaMemset(error flag)");
+    }
     if (!rc) rc = p->fp64 ? make_spectra<double>(p) : make_spectra<float>(p);
     if (rc) {
         free_plan(p);
@@ -419,6 +425,24 @@ int grav_kernel_values(int nx, int ny, int nz, double dx, double dy, double dz, 
     Geometry g{nx, ny, nz, dx, dy, dz, h};
     cudaError_t e = launch_kernel_gen(g, components & 0x7Fu, 0, nz, 1, 0, 0, K_dev, (cudaStream_t)stream);
     if (e != cudaSuccess) return cuda_fail(e, "kernel generation launch");
+    return GRAV_OK;
+}
+
+int grav_plan_check(grav_plan* plan) {
+    if (!plan) {
+        set_error("grav_plan_check: null plan");
+        return GRAV_EINVAL;
+    }
+    cudaError_t e = cudaDeviceSynchronize();
+    if (e != cudaSuccess) return cuda_fail(e, "cudaDeviceSynchronize");
+    int flag = 0;
+    e = cudaMemcpy(&flag, plan->err_flag, sizeof(int), cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaMemcpy(error flag)");
+    if (flag) {
+        cudaMemset(plan->err_flag, 0, sizeof(int));
+        set_error("a pipeline wait of an earlier call on this plan ran out; its output is invalid");
+        return GRAV_ETIMEOUT;
+    }
     return GRAV_OK;
 }
 

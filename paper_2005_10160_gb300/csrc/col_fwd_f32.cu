@@ -2,5 +2,5 @@
 #include "spectral_launch.cuh"
 
 namespace grav {
-GRAV_COLUMN_LAUNCHER(launch_forward_columns, forward_impl, float)
+GRAV_FORWARD_LAUNCHER(float)
 }  // namespace grav

@@ -138,6 +138,164 @@ __device__ __forceinline__ void fft_pass(C* buf, int sstr, int ls, const C* __re
     __syncthreads();
 }
 
+// Per-pass twiddle tables.  Pass p >= 1 of a 2^LOGN transform multiplies
+// input r of butterfly k (k < ls) by W_{ls R}^{r k}; the table keeps these at
+// tab[tw_tab_off(p) + (r - 1) ls + k], so the threads of a warp (consecutive
+// k) read consecutive entries, or one broadcast entry when ls is small.
+__host__ __device__ constexpr int tw_tab_off(int logn, int p) {
+    int off = 0;
+    for (int q = 1; q < p; ++q) off += pass_ls(logn, q) * (pass_radix(logn, q) - 1);
+    return off;
+}
+__host__ __device__ constexpr int tw_tab_len(int logn) { return tw_tab_off(logn, num_passes(logn)); }
+
+// Fill the table from W_T (T = N << tw_shift); all threads of the block call it.
+template <typename C, int LOGN, int NT>
+__device__ __forceinline__ void build_tw_tab(C* tab, const C* __restrict__ tw, int tw_shift, int tid) {
+    constexpr int N = 1 << LOGN;
+#pragma unroll
+    for (int p = 1; p < num_passes(LOGN); ++p) {
+        const int ls = pass_ls(LOGN, p), R = pass_radix(LOGN, p), off = tw_tab_off(LOGN, p);
+        for (int e = tid; e < ls * (R - 1); e += NT) {
+            const int r = e / ls + 1, k = e - (r - 1) * ls;
+            tab[off + e] = tw[(r * k * (N / (ls * R))) << tw_shift];
+        }
+    }
+}
+
+// Stockham pass p >= 1 with twiddles from the per-pass table.
+template <typename C, int LOGN, int P, int NSEQ, int NT, bool INV>
+__device__ __forceinline__ void fft_pass_tab(C* buf, int sstr, const C* tab, int tid) {
+    constexpr int N = 1 << LOGN;
+    constexpr int R = pass_radix(LOGN, P);
+    constexpr int LS = pass_ls(LOGN, P);
+    constexpr int OFF = tw_tab_off(LOGN, P);
+    constexpr int NR = N / R;
+    constexpr int TOTAL = NSEQ * NR;
+    constexpr int BPT = (TOTAL + NT - 1) / NT;
+    C u[BPT][R];
+#pragma unroll
+    for (int b = 0; b < BPT; ++b) {
+        const int g = tid + b * NT;
+        if (tid < NT && g < TOTAL) {
+            const int s = g / NR, i = g - s * NR;
+            const C* x = buf + s * sstr;
+#pragma unroll
+            for (int r = 0; r < R; ++r) u[b][r] = x[sidx<C>(i + r * NR)];
+        }
+    }
+    __syncthreads();
+#pragma unroll
+    for (int b = 0; b < BPT; ++b) {
+        const int g = tid + b * NT;
+        if (tid < NT && g < TOTAL) {
+            const int s = g / NR, i = g - s * NR;
+            const int k = i & (LS - 1);
+#pragma unroll
+            for (int r = 1; r < R; ++r) {
+                C w = tab[OFF + (r - 1) * LS + k];
+                if (INV) w.y = -w.y;
+                u[b][r] = cmul(u[b][r], w);
+            }
+            dftR<C, R, INV>(u[b]);
+            C* y = buf + s * sstr;
+            const int j = (i - k) * R + k;
+#pragma unroll
+            for (int r = 0; r < R; ++r) y[sidx<C>(j + r * LS)] = u[b][r];
+        }
+    }
+    __syncthreads();
+}
+
+template <typename C, int LOGN, int NSEQ, int NT, bool INV>
+__device__ __forceinline__ void fft_tail_tab(C* buf, int sstr, const C* tab, int tid) {
+    constexpr int NP = num_passes(LOGN);
+    if constexpr (NP > 1) fft_pass_tab<C, LOGN, 1, NSEQ, NT, INV>(buf, sstr, tab, tid);
+    if constexpr (NP > 2) fft_pass_tab<C, LOGN, 2, NSEQ, NT, INV>(buf, sstr, tab, tid);
+    if constexpr (NP > 3) fft_pass_tab<C, LOGN, 3, NSEQ, NT, INV>(buf, sstr, tab, tid);
+    if constexpr (NP > 4) fft_pass_tab<C, LOGN, 4, NSEQ, NT, INV>(buf, sstr, tab, tid);
+}
+
+// First Stockham pass (no twiddles) taking its inputs from a functor
+// load(s, m) -> element m of sequence s, and writing to the shared buffer.
+template <typename C, int LOGN, int R, int NSEQ, int NT, bool INV, typename Load>
+__device__ __forceinline__ void fft_first_pass_from(C* buf, int sstr, int tid, Load load) {
+    constexpr int N = 1 << LOGN;
+    constexpr int NR = N / R;
+    constexpr int TOTAL = NSEQ * NR;
+    constexpr int BPT = (TOTAL + NT - 1) / NT;
+#pragma unroll
+    for (int b = 0; b < BPT; ++b) {
+        const int g = tid + b * NT;
+        if (tid < NT && g < TOTAL) {
+            const int s = g / NR, i = g - s * NR;
+            C u[R];
+#pragma unroll
+            for (int r = 0; r < R; ++r) u[r] = load(s, i + r * NR);
+            dftR<C, R, INV>(u);
+            C* y = buf + s * sstr;
+#pragma unroll
+            for (int r = 0; r < R; ++r) y[sidx<C>(i * R + r)] = u[r];
+        }
+    }
+    __syncthreads();
+}
+
+// FFT of NSEQ sequences whose inputs come from load(s, m); the result is in
+// buf (natural order).
+template <typename C, int LOGN, int NSEQ, int NT, bool INV, typename Load>
+__device__ __forceinline__ void block_fft_from(C* buf, int sstr, const C* __restrict__ tw, int tw_shift, int tid,
+                                               Load load) {
+    constexpr int NP = num_passes(LOGN);
+    static_assert(NP <= 5, "transform too long");
+    fft_first_pass_from<C, LOGN, pass_radix(LOGN, 0), NSEQ, NT, INV>(buf, sstr, tid, load);
+    if constexpr (NP > 1) fft_pass<C, LOGN, pass_radix(LOGN, 1), NSEQ, NT, INV>(buf, sstr, pass_ls(LOGN, 1), tw, tw_shift, tid);
+    if constexpr (NP > 2) fft_pass<C, LOGN, pass_radix(LOGN, 2), NSEQ, NT, INV>(buf, sstr, pass_ls(LOGN, 2), tw, tw_shift, tid);
+    if constexpr (NP > 3) fft_pass<C, LOGN, pass_radix(LOGN, 3), NSEQ, NT, INV>(buf, sstr, pass_ls(LOGN, 3), tw, tw_shift, tid);
+    if constexpr (NP > 4) fft_pass<C, LOGN, pass_radix(LOGN, 4), NSEQ, NT, INV>(buf, sstr, pass_ls(LOGN, 4), tw, tw_shift, tid);
+}
+
+// The same with table twiddles: inputs from load(s, m), result in buf.
+template <typename C, int LOGN, int NSEQ, int NT, bool INV, typename Load>
+__device__ __forceinline__ void block_fft_tab_from(C* buf, int sstr, const C* tab, int tid, Load load) {
+    static_assert(num_passes(LOGN) <= 5, "transform too long");
+    fft_first_pass_from<C, LOGN, pass_radix(LOGN, 0), NSEQ, NT, INV>(buf, sstr, tid, load);
+    fft_tail_tab<C, LOGN, NSEQ, NT, INV>(buf, sstr, tab, tid);
+}
+
+// In-place FFT of NSEQ sequences in buf with table twiddles.
+template <typename C, int LOGN, int NSEQ, int NT, bool INV>
+__device__ __forceinline__ void block_fft_tab(C* buf, int sstr, const C* tab, int tid) {
+    constexpr int N = 1 << LOGN;
+    constexpr int R = pass_radix(LOGN, 0);
+    constexpr int NR = N / R;
+    constexpr int TOTAL = NSEQ * NR;
+    constexpr int BPT = (TOTAL + NT - 1) / NT;
+    C u[BPT][R];
+#pragma unroll
+    for (int b = 0; b < BPT; ++b) {
+        const int g = tid + b * NT;
+        if (tid < NT && g < TOTAL) {
+            const int s = g / NR, i = g - s * NR;
+#pragma unroll
+            for (int r = 0; r < R; ++r) u[b][r] = buf[s * sstr + sidx<C>(i + r * NR)];
+        }
+    }
+    __syncthreads();
+#pragma unroll
+    for (int b = 0; b < BPT; ++b) {
+        const int g = tid + b * NT;
+        if (tid < NT && g < TOTAL) {
+            const int s = g / NR, i = g - s * NR;
+            dftR<C, R, INV>(u[b]);
+#pragma unroll
+            for (int r = 0; r < R; ++r) buf[s * sstr + sidx<C>(i * R + r)] = u[b][r];
+        }
+    }
+    __syncthreads();
+    fft_tail_tab<C, LOGN, NSEQ, NT, INV>(buf, sstr, tab, tid);
+}
+
 // Full in-place FFT of NSEQ sequences of 2^LOGN points in shared memory
 // (natural order in, natural order out).  tw is W_T with T = N << tw_shift.
 template <typename C, int LOGN, int NSEQ, int NT, bool INV>

@@ -69,6 +69,7 @@ struct grav_plan {
     void* ws_a;     // workspace: forward row transforms / adjoint column outputs
     void* ws_b;     // workspace: forward column outputs / adjoint row transforms
     size_t spec_bytes, tw_bytes, ws_a_bytes, ws_b_bytes;
+    int* err_flag;  // device int: a pipeline wait ran out
     int device;
     // stage timing (grav_plan_set_timing)
     int timing;
@@ -109,16 +110,18 @@ cudaError_t launch_row_c2r(int log_p, const void* in0, const void* in1, int I, i
                            cudaStream_t s);
 
 // ---- column kernels (spectral.cuh, col_*.cu) ----
+// err: device int set to 1 when a pipeline wait ran out (the kernel then
+// leaves early and its output is invalid).
 template <typename R>
 cudaError_t launch_forward_columns(int log_n, const ColumnArgs& a, const void* X, const R* spec,
-                                   void* Y, const void* tw, cudaStream_t s);
+                                   void* Y, const void* tw, int* err, cudaStream_t s);
 template <typename R>
 cudaError_t launch_adjoint_columns(int log_n, const ColumnArgs& a, const void* Xr, const R* spec,
                                    void* Z, const void* tw, cudaStream_t s);
 template <> cudaError_t launch_forward_columns<float>(int, const ColumnArgs&, const void*, const float*, void*,
-                                                     const void*, cudaStream_t);
+                                                     const void*, int*, cudaStream_t);
 template <> cudaError_t launch_forward_columns<double>(int, const ColumnArgs&, const void*, const double*, void*,
-                                                      const void*, cudaStream_t);
+                                                      const void*, int*, cudaStream_t);
 template <> cudaError_t launch_adjoint_columns<float>(int, const ColumnArgs&, const void*, const float*, void*,
                                                      const void*, cudaStream_t);
 template <> cudaError_t launch_adjoint_columns<double>(int, const ColumnArgs&, const void*, const double*, void*,

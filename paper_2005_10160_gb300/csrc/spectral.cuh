@@ -11,17 +11,19 @@
 // imaginary and even or odd in ky because the embedded kernel is exactly
 // even or odd under reflection (Sec. 2.2).
 //
-// Forward (Eq. 21): for every layer n the CTA transforms the density column,
-// multiplies by S_{c,n} and accumulates over n in registers (FP32 with a
-// Kahan-compensated layer sum, or FP64); at the end it inverse-transforms
-// each component's accumulator and writes the rows y < ny.  The threads are
-// split into two groups that own different components, so each thread keeps
-// the accumulators of at most CPG components for H mirror pairs.
+// Forward (Eq. 21): the row transforms of each layer's column and that
+// layer's spectra slab stream into a shared-memory ring through bulk
+// asynchronous copies; NSEQ layers at a time are transformed, multiplied by
+// S_{c,n} and accumulated over n in registers (FP32 with a Kahan-compensated
+// layer sum, or FP64).  Each thread owns one mirror pair (two bins) for every
+// component.  At the end each component's accumulator is inverse-
+// transformed and the rows y < ny are written.
 //
 // Adjoint (transpose of Eq. 21): the residual of every component is
 // transformed once; per layer the CTA forms sum_c conj(S_{c,n}) R_c,
 // inverse-transforms it and writes that layer's rows.
 #pragma once
+#include "async_copy.cuh"
 #include "fft_block.cuh"
 #include "grav_internal.h"
 
@@ -63,118 +65,179 @@ template <typename R> __device__ __forceinline__ void kahan_add(R& sum, R& comp,
     sum = t;
 }
 
-template <typename R, int LOGN, int CPG, bool KAHAN>
-__global__ void __launch_bounds__(ColShape<LOGN>::NT, 1)
-    forward_column_kernel(ColumnArgs a, const typename cplx<R>::type* __restrict__ X, const R* __restrict__ spec,
-                          typename cplx<R>::type* __restrict__ Y, const typename cplx<R>::type* __restrict__ tw) {
+// Shared-memory layout of the forward column kernel, chosen on the host.
+// A ring of `depth` stages, each holding one layer's row-transform column
+// (x_bytes) and that layer's kernel-spectra slab (s_bytes), is filled by
+// bulk copies; NSEQ layers are transformed per round in the FFT buffers.
+struct FwdSmem {
+    int depth;
+    uint32_t x_bytes, s_bytes, stage_bytes;
+    uint32_t fft_off, tw_off, bar_off, total;
+};
+
+template <typename R> struct FwdCfg {
+    static constexpr int NSEQ = sizeof(R) == 4 ? 4 : 2;  // layers per round
+};
+
+// Forward column stage, one CTA per (kx, r) with blockIdx.x = 2 kx + r (the
+// two parities of a column run side by side and share its row transforms
+// through L2).  Thread q owns mirror pair q and accumulates every component
+// for both of its bins; thread 0 also issues the bulk copies.
+//
+// The per-layer product is S v with S = s or i s (imaginary spectra) and,
+// for the mirror bin, S = +-s (odd components).  Both factors are constant
+// over the layers, so the loop accumulates s v for every component and the
+// epilogue applies i and the sign once: sum_n (i s_n) v_n = i sum_n s_n v_n.
+// The layer sum is compensated per round of NSEQ layers: the round's terms
+// are added in plain arithmetic and the round total enters a Kahan sum.
+template <typename R, int LOGN, int NC>
+__global__ void __launch_bounds__(ColShape<LOGN>::J, 1)
+    forward_column_kernel(ColumnArgs a, FwdSmem L, const typename cplx<R>::type* __restrict__ X,
+                          const R* __restrict__ spec, typename cplx<R>::type* __restrict__ Y,
+                          const typename cplx<R>::type* __restrict__ tw, int* __restrict__ err) {
     using C = typename cplx<R>::type;
-    using S = ColShape<LOGN>;
-    constexpr int N = S::N, J = S::J, H = S::H, TG = S::TG, NT = S::NT, XPT = S::XPT;
+    constexpr int N = 1 << LOGN, J = ColShape<LOGN>::J, NT = J;
+    constexpr int NSEQ = FwdCfg<R>::NSEQ;
+    constexpr bool KAHAN = sizeof(R) == 4;
     constexpr int SSTR = spad_len<C>(N);
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    C* buf = reinterpret_cast<C*>(smem_raw);
+    extern __shared__ __align__(128) unsigned char smem[];
+    uint64_t* bars = reinterpret_cast<uint64_t*>(smem + L.bar_off);
+    C* fbuf = reinterpret_cast<C*>(smem + L.fft_off);
+    C* tws = reinterpret_cast<C*>(smem + L.tw_off);  // fold twiddles W_Py^m, m < N
+    C* ttab = tws + N;                                  // per-pass FFT twiddles
 
     const int tid = threadIdx.x;
-    const int g = tid / TG, lt = tid - g * TG;
-    const int kx = blockIdx.x, r = blockIdx.y;
-    const C* Xc = X + (size_t)kx * a.nz * a.ny_pad;
-    const R* sp = spec + (size_t)(r * a.kx_count + kx) * a.nz * a.ncomp * a.jp;
-    const bool has_nyq = (r == 0 && lt == 0);
+    const int r = blockIdx.x & 1, kx = blockIdx.x >> 1;
+    const int nz = a.nz, ny = a.ny;
+    const C* Xk = X + (size_t)kx * nz * a.ny_pad;
+    const size_t s_row = (size_t)a.ncomp * a.jp;
+    const R* Sk = spec + (size_t)(r * a.kx_count + kx) * nz * s_row;
+    auto stage_x = [&](int s) { return reinterpret_cast<const C*>(smem + (size_t)s * L.stage_bytes); };
+    auto stage_s = [&](int s) { return reinterpret_cast<const R*>(smem + (size_t)s * L.stage_bytes + L.x_bytes); };
+    auto issue = [&](int n) {
+        const int s = n % L.depth;
+        unsigned char* dst = smem + (size_t)s * L.stage_bytes;
+        mbar_arrive_expect_tx(&bars[s], L.x_bytes + L.s_bytes);
+        bulk_g2s(dst, Xk + (size_t)n * a.ny_pad, L.x_bytes, &bars[s]);
+        bulk_g2s(dst + L.x_bytes, Sk + (size_t)n * s_row, L.s_bytes, &bars[s]);
+    };
 
-    R acc[CPG][H][2][2];
-    R cmp[CPG][H][2][2];
+    if (tid == 0) {
+        for (int s = 0; s < L.depth; ++s) mbar_init(&bars[s], 1);
+        fence_mbar_init();
+    }
+    for (int e = tid; e < N; e += NT) tws[e] = tw[e << a.tw_shift_p];
+    build_tw_tab<C, LOGN, NT>(ttab, tw, a.tw_shift_n, tid);
+    __syncthreads();
+    const int first = nz < L.depth ? nz : L.depth;
+    if (tid == 0)
+        for (int n = 0; n < first; ++n) issue(n);
+
+    R acc[NC][4], cmp[NC][4];
 #pragma unroll
-    for (int c = 0; c < CPG; ++c)
+    for (int c = 0; c < NC; ++c)
 #pragma unroll
-        for (int s = 0; s < H; ++s)
-#pragma unroll
-            for (int m = 0; m < 2; ++m) {
-                acc[c][s][m][0] = acc[c][s][m][1] = 0;
-                cmp[c][s][m][0] = cmp[c][s][m][1] = 0;
+        for (int j = 0; j < 4; ++j) acc[c][j] = cmp[c][j] = 0;
+    const int q = tid;
+    int k1, k2;
+    pair_pos<N>(q, r, k1, k2);
+    const bool nyq = (r == 0 && q == 0);
+
+    for (int n0 = 0; n0 < nz; n0 += NSEQ) {
+        const int cnt = nz - n0 < NSEQ ? nz - n0 : NSEQ;
+        bool ok = true;
+        for (int l = 0; l < cnt; ++l) {
+            const int n = n0 + l;
+            ok = ok && mbar_wait_bounded(&bars[n % L.depth], (uint32_t)((n / L.depth) & 1), kWaitLimitNs);
+        }
+        if (__syncthreads_or(!ok)) {
+            // A copy never arrived: record it, let the copies still in
+            // flight land (bounded), and leave.
+            if (tid == 0) {
+                atomicExch(err, 1);
+                const int last = n0 + L.depth < nz ? n0 + L.depth : nz;
+                for (int n = n0; n < last; ++n)
+                    mbar_wait_bounded(&bars[n % L.depth], (uint32_t)((n / L.depth) & 1), kWaitLimitNs);
             }
-
-    C xv[XPT];
-    R sv[CPG][H], se[CPG];
-    auto load_x = [&](int n) {
-#pragma unroll
-        for (int j = 0; j < XPT; ++j) {
-            const int m = tid + j * NT;
-            xv[j] = (m < a.ny) ? Xc[(size_t)n * a.ny_pad + m] : cmk<C>(0, 0);
+            return;
         }
-    };
-    auto load_s = [&](int n) {
+        // Column FFTs of the round's layers; the first pass reads the staged
+        // rows and folds them for ky parity r: a[m] = x[m] W_Py^(m r).
+        block_fft_tab_from<C, LOGN, NSEQ, NT, false>(fbuf, SSTR, ttab, tid, [&](int l, int m) {
+            C v = cmk<C>(0, 0);
+            if (l < cnt && m < ny) {
+                v = stage_x((n0 + l) % L.depth)[m];
+                if (r) v = cmul(v, tws[m]);
+            }
+            return v;
+        });
+        R part[NC][4];
 #pragma unroll
-        for (int c = 0; c < CPG; ++c) {
-            const int slot = g * CPG + c;
-            const R* row = sp + ((size_t)n * a.ncomp + slot) * a.jp;
+        for (int c = 0; c < NC; ++c)
 #pragma unroll
-            for (int s = 0; s < H; ++s) sv[c][s] = (slot < a.ncomp) ? row[lt * H + s] : (R)0;
-            se[c] = (slot < a.ncomp && has_nyq) ? row[J] : (R)0;
-        }
-    };
-    load_x(0);
-    load_s(0);
-
-    for (int n = 0; n < a.nz; ++n) {
-        // fold for ky parity r: a[m] = x[m] W_Py^(m r)
+            for (int j = 0; j < 4; ++j) part[c][j] = 0;
+        for (int l = 0; l < cnt; ++l) {
+            const C v1 = fbuf[l * SSTR + sidx<C>(k1)], v2 = fbuf[l * SSTR + sidx<C>(k2)];
+            const R* Ss = stage_s((n0 + l) % L.depth) + q;
 #pragma unroll
-        for (int j = 0; j < XPT; ++j) {
-            const int m = tid + j * NT;
-            if (m < N) buf[sidx<C>(m)] = r ? cmul(xv[j], tw[m << a.tw_shift_p]) : xv[j];
-        }
-        if (n + 1 < a.nz) load_x(n + 1);  // in flight during this layer's FFT
-        __syncthreads();
-        block_fft<C, LOGN, 1, NT, false>(buf, SSTR, tw, a.tw_shift_n, tid);
-#pragma unroll
-        for (int s = 0; s < H; ++s) {
-            const int q = lt * H + s;
-            int k1, k2;
-            pair_pos<N>(q, r, k1, k2);
-            const C v1 = buf[sidx<C>(k1)], v2 = buf[sidx<C>(k2)];
-#pragma unroll
-            for (int c = 0; c < CPG; ++c) {
-                const int slot = g * CPG + c;
-                const bool imag = (a.imag_mask >> slot) & 1u;
-                const R s1 = sv[c][s];
-                const R s2 = (r == 0 && q == 0) ? se[c] : (((a.oddv_mask >> slot) & 1u) ? -s1 : s1);
-                const C t1 = spec_term<C>(s1, v1, imag), t2 = spec_term<C>(s2, v2, imag);
-                if (KAHAN) {
-                    kahan_add(acc[c][s][0][0], cmp[c][s][0][0], t1.x);
-                    kahan_add(acc[c][s][0][1], cmp[c][s][0][1], t1.y);
-                    kahan_add(acc[c][s][1][0], cmp[c][s][1][0], t2.x);
-                    kahan_add(acc[c][s][1][1], cmp[c][s][1][1], t2.y);
-                } else {
-                    acc[c][s][0][0] += t1.x; acc[c][s][0][1] += t1.y;
-                    acc[c][s][1][0] += t2.x; acc[c][s][1][1] += t2.y;
+            for (int c = 0; c < NC; ++c) {
+                if (c < a.ncomp) {
+                    const R s1 = Ss[c * a.jp];
+                    const R s2 = nyq ? Ss[c * a.jp + J] : s1;
+                    part[c][0] += s1 * v1.x;
+                    part[c][1] += s1 * v1.y;
+                    part[c][2] += s2 * v2.x;
+                    part[c][3] += s2 * v2.y;
                 }
             }
         }
-        if (n + 1 < a.nz) load_s(n + 1);  // in flight during the next layer's FFT
-        __syncthreads();
+#pragma unroll
+        for (int c = 0; c < NC; ++c)
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+                if (KAHAN) kahan_add(acc[c][j], cmp[c][j], part[c][j]);
+                else acc[c][j] += part[c][j];
+            }
+        __syncthreads();  // stages and FFT buffers free again
+        if (tid == 0) {
+            fence_proxy_async_smem();
+            for (int l = 0; l < cnt; ++l)
+                if (n0 + l + L.depth < nz) issue(n0 + l + L.depth);
+        }
     }
 
-    // Inverse column transform of every component, crop to y < ny.
-    C* gb = buf + g * SSTR;
+    // Apply i (imaginary spectra) and the mirror sign (odd in y), then the
+    // inverse column transforms, NSEQ components per round; crop to y < ny.
 #pragma unroll
-    for (int c = 0; c < CPG; ++c) {
-        const int slot = g * CPG + c;
+    for (int c0 = 0; c0 < NC; c0 += NSEQ) {
 #pragma unroll
-        for (int s = 0; s < H; ++s) {
-            int k1, k2;
-            pair_pos<N>(lt * H + s, r, k1, k2);
-            R e0 = acc[c][s][0][0], e1 = acc[c][s][0][1], e2 = acc[c][s][1][0], e3 = acc[c][s][1][1];
-            if (KAHAN) { e0 -= cmp[c][s][0][0]; e1 -= cmp[c][s][0][1]; e2 -= cmp[c][s][1][0]; e3 -= cmp[c][s][1][1]; }
-            gb[sidx<C>(k1)] = cmk<C>(e0, e1);
-            gb[sidx<C>(k2)] = cmk<C>(e2, e3);
+        for (int l = 0; l < NSEQ; ++l) {
+            const int c = c0 + l;
+            if (c < NC) {
+                R e[4];
+#pragma unroll
+                for (int j = 0; j < 4; ++j) e[j] = KAHAN ? acc[c][j] - cmp[c][j] : acc[c][j];
+                const bool imag = (a.imag_mask >> c) & 1u;
+                const bool flip = !nyq && ((a.oddv_mask >> c) & 1u);
+                C b1 = cmk<C>(e[0], e[1]), b2 = cmk<C>(e[2], e[3]);
+                if (flip) b2 = cmk<C>(-b2.x, -b2.y);
+                if (imag) {
+                    b1 = cmk<C>(-b1.y, b1.x);
+                    b2 = cmk<C>(-b2.y, b2.x);
+                }
+                fbuf[l * SSTR + sidx<C>(k1)] = b1;
+                fbuf[l * SSTR + sidx<C>(k2)] = b2;
+            }
         }
         __syncthreads();
-        block_fft<C, LOGN, 1, TG, true>(gb, SSTR, tw, a.tw_shift_n, lt);
-        if (slot < a.ncomp) {
-            C* dst = Y + ((size_t)(r * a.kx_count + kx) * a.ncomp + slot) * a.ny_pad;
-            for (int y = lt; y < a.ny; y += TG) {
-                C v = gb[sidx<C>(y)];
-                if (r) v = cmul(v, cconj(tw[y << a.tw_shift_p]));
-                dst[y] = v;
+        block_fft_tab<C, LOGN, NSEQ, NT, true>(fbuf, SSTR, ttab, tid);
+        for (int e = tid; e < NSEQ * ny; e += NT) {
+            const int l = e / ny, y = e - l * ny;
+            const int c = c0 + l;
+            if (c < a.ncomp) {
+                C v = fbuf[l * SSTR + sidx<C>(y)];
+                if (r) v = cmul(v, cconj(tws[y]));
+                Y[((size_t)(r * a.kx_count + kx) * a.ncomp + c) * a.ny_pad + y] = v;
             }
         }
         __syncthreads();
@@ -306,6 +369,33 @@ size_t column_smem_bytes(int log_n) {
     return 2 * (size_t)spad_len<C>(1 << log_n) * sizeof(C);
 }
 
+// Ring depth and offsets for the forward column kernel; depth is 0 when even
+// NSEQ stages do not fit in the shared memory a CTA may use.
+template <typename R>
+FwdSmem forward_smem(int log_n, int ny_pad, int ncomp, int jp, int max_bytes) {
+    using C = typename cplx<R>::type;
+    constexpr int NSEQ = FwdCfg<R>::NSEQ;
+    FwdSmem L{};
+    L.x_bytes = (uint32_t)(ny_pad * sizeof(C));
+    L.s_bytes = (uint32_t)(ncomp * jp * sizeof(R));
+    L.stage_bytes = (L.x_bytes + L.s_bytes + 127u) & ~127u;
+    const uint32_t fft_bytes = (uint32_t)(NSEQ * spad_len<C>(1 << log_n) * sizeof(C));
+    const uint32_t tw_bytes = (uint32_t)(((1u << log_n) + tw_tab_len(log_n)) * sizeof(C));
+    int depth = 2 * NSEQ;
+    while (depth >= NSEQ && (size_t)depth * L.stage_bytes + fft_bytes + tw_bytes + depth * 8 + 128 > (size_t)max_bytes)
+        --depth;
+    if (depth < NSEQ) return FwdSmem{};
+    L.depth = depth;
+    L.fft_off = depth * L.stage_bytes;
+    L.tw_off = L.fft_off + fft_bytes;
+    L.bar_off = (L.tw_off + tw_bytes + 7u) & ~7u;
+    L.total = L.bar_off + depth * 8;
+    return L;
+}
+
 inline int cpg_for(int ncomp) { return (ncomp + 1) / 2; }
+
+// Components per thread instantiated for the forward kernel.
+inline int nc_for(int ncomp) { return ncomp == 5 ? 6 : ncomp; }
 
 }  // namespace grav

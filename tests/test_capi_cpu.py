@@ -57,3 +57,8 @@ def test_null_plan_and_buffers_are_rejected(gravlib):
     L.grav_plan_destroy(None)
     assert L.grav_kernel_values(4, 4, 1, 1.0, 1.0, 1.0, 1.0, 1, None, None) == capi.GRAV_EINVAL
     assert L.grav_kernel_values(4, 4, 1, 1.0, 1.0, 1.0, -1.0, 1, None, None) == capi.GRAV_EINVAL
+    assert L.grav_plan_check(None) == capi.GRAV_EINVAL
+    assert L.grav_plan_set_timing(None, 1) == capi.GRAV_EINVAL
+    assert L.grav_forward_static_scratch(None, None, None, None) == capi.GRAV_EINVAL
+    rc, _ = capi.grav_selftest_bounded_wait(0.0)
+    assert rc == capi.GRAV_EINVAL
