@@ -138,6 +138,18 @@ __device__ __forceinline__ void fft_pass(C* buf, int sstr, int ls, const C* __re
     __syncthreads();
 }
 
+// Barrier over the whole block.
+struct BlockSync {
+    __device__ __forceinline__ void operator()() const { __syncthreads(); }
+};
+// Named barrier `id` (1..15) over `count` threads (whole warps) of the block.
+struct GroupSync {
+    int id, count;
+    __device__ __forceinline__ void operator()() const {
+        asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(count) : "memory");
+    }
+};
+
 // Per-pass twiddle tables.  Pass p >= 1 of a 2^LOGN transform multiplies
 // input r of butterfly k (k < ls) by W_{ls R}^{r k}; the table keeps these at
 // tab[tw_tab_off(p) + (r - 1) ls + k], so the threads of a warp (consecutive
@@ -164,8 +176,8 @@ __device__ __forceinline__ void build_tw_tab(C* tab, const C* __restrict__ tw, i
 }
 
 // Stockham pass p >= 1 with twiddles from the per-pass table.
-template <typename C, int LOGN, int P, int NSEQ, int NT, bool INV>
-__device__ __forceinline__ void fft_pass_tab(C* buf, int sstr, const C* tab, int tid) {
+template <typename C, int LOGN, int P, int NSEQ, int NT, bool INV, typename Sync = BlockSync>
+__device__ __forceinline__ void fft_pass_tab(C* buf, int sstr, const C* tab, int tid, Sync sync = Sync()) {
     constexpr int N = 1 << LOGN;
     constexpr int R = pass_radix(LOGN, P);
     constexpr int LS = pass_ls(LOGN, P);
@@ -184,7 +196,7 @@ __device__ __forceinline__ void fft_pass_tab(C* buf, int sstr, const C* tab, int
             for (int r = 0; r < R; ++r) u[b][r] = x[sidx<C>(i + r * NR)];
         }
     }
-    __syncthreads();
+    sync();
 #pragma unroll
     for (int b = 0; b < BPT; ++b) {
         const int g = tid + b * NT;
@@ -204,22 +216,22 @@ __device__ __forceinline__ void fft_pass_tab(C* buf, int sstr, const C* tab, int
             for (int r = 0; r < R; ++r) y[sidx<C>(j + r * LS)] = u[b][r];
         }
     }
-    __syncthreads();
+    sync();
 }
 
-template <typename C, int LOGN, int NSEQ, int NT, bool INV>
-__device__ __forceinline__ void fft_tail_tab(C* buf, int sstr, const C* tab, int tid) {
+template <typename C, int LOGN, int NSEQ, int NT, bool INV, typename Sync = BlockSync>
+__device__ __forceinline__ void fft_tail_tab(C* buf, int sstr, const C* tab, int tid, Sync sync = Sync()) {
     constexpr int NP = num_passes(LOGN);
-    if constexpr (NP > 1) fft_pass_tab<C, LOGN, 1, NSEQ, NT, INV>(buf, sstr, tab, tid);
-    if constexpr (NP > 2) fft_pass_tab<C, LOGN, 2, NSEQ, NT, INV>(buf, sstr, tab, tid);
-    if constexpr (NP > 3) fft_pass_tab<C, LOGN, 3, NSEQ, NT, INV>(buf, sstr, tab, tid);
-    if constexpr (NP > 4) fft_pass_tab<C, LOGN, 4, NSEQ, NT, INV>(buf, sstr, tab, tid);
+    if constexpr (NP > 1) fft_pass_tab<C, LOGN, 1, NSEQ, NT, INV>(buf, sstr, tab, tid, sync);
+    if constexpr (NP > 2) fft_pass_tab<C, LOGN, 2, NSEQ, NT, INV>(buf, sstr, tab, tid, sync);
+    if constexpr (NP > 3) fft_pass_tab<C, LOGN, 3, NSEQ, NT, INV>(buf, sstr, tab, tid, sync);
+    if constexpr (NP > 4) fft_pass_tab<C, LOGN, 4, NSEQ, NT, INV>(buf, sstr, tab, tid, sync);
 }
 
 // First Stockham pass (no twiddles) taking its inputs from a functor
 // load(s, m) -> element m of sequence s, and writing to the shared buffer.
-template <typename C, int LOGN, int R, int NSEQ, int NT, bool INV, typename Load>
-__device__ __forceinline__ void fft_first_pass_from(C* buf, int sstr, int tid, Load load) {
+template <typename C, int LOGN, int R, int NSEQ, int NT, bool INV, typename Load, typename Sync = BlockSync>
+__device__ __forceinline__ void fft_first_pass_from(C* buf, int sstr, int tid, Load load, Sync sync = Sync()) {
     constexpr int N = 1 << LOGN;
     constexpr int NR = N / R;
     constexpr int TOTAL = NSEQ * NR;
@@ -238,7 +250,7 @@ __device__ __forceinline__ void fft_first_pass_from(C* buf, int sstr, int tid, L
             for (int r = 0; r < R; ++r) y[sidx<C>(i * R + r)] = u[r];
         }
     }
-    __syncthreads();
+    sync();
 }
 
 // FFT of NSEQ sequences whose inputs come from load(s, m); the result is in
@@ -256,16 +268,17 @@ __device__ __forceinline__ void block_fft_from(C* buf, int sstr, const C* __rest
 }
 
 // The same with table twiddles: inputs from load(s, m), result in buf.
-template <typename C, int LOGN, int NSEQ, int NT, bool INV, typename Load>
-__device__ __forceinline__ void block_fft_tab_from(C* buf, int sstr, const C* tab, int tid, Load load) {
+template <typename C, int LOGN, int NSEQ, int NT, bool INV, typename Load, typename Sync = BlockSync>
+__device__ __forceinline__ void block_fft_tab_from(C* buf, int sstr, const C* tab, int tid, Load load,
+                                                   Sync sync = Sync()) {
     static_assert(num_passes(LOGN) <= 5, "transform too long");
-    fft_first_pass_from<C, LOGN, pass_radix(LOGN, 0), NSEQ, NT, INV>(buf, sstr, tid, load);
-    fft_tail_tab<C, LOGN, NSEQ, NT, INV>(buf, sstr, tab, tid);
+    fft_first_pass_from<C, LOGN, pass_radix(LOGN, 0), NSEQ, NT, INV>(buf, sstr, tid, load, sync);
+    fft_tail_tab<C, LOGN, NSEQ, NT, INV>(buf, sstr, tab, tid, sync);
 }
 
 // In-place FFT of NSEQ sequences in buf with table twiddles.
-template <typename C, int LOGN, int NSEQ, int NT, bool INV>
-__device__ __forceinline__ void block_fft_tab(C* buf, int sstr, const C* tab, int tid) {
+template <typename C, int LOGN, int NSEQ, int NT, bool INV, typename Sync = BlockSync>
+__device__ __forceinline__ void block_fft_tab(C* buf, int sstr, const C* tab, int tid, Sync sync = Sync()) {
     constexpr int N = 1 << LOGN;
     constexpr int R = pass_radix(LOGN, 0);
     constexpr int NR = N / R;
@@ -281,7 +294,7 @@ __device__ __forceinline__ void block_fft_tab(C* buf, int sstr, const C* tab, in
             for (int r = 0; r < R; ++r) u[b][r] = buf[s * sstr + sidx<C>(i + r * NR)];
         }
     }
-    __syncthreads();
+    sync();
 #pragma unroll
     for (int b = 0; b < BPT; ++b) {
         const int g = tid + b * NT;
@@ -292,8 +305,8 @@ __device__ __forceinline__ void block_fft_tab(C* buf, int sstr, const C* tab, in
             for (int r = 0; r < R; ++r) buf[s * sstr + sidx<C>(i * R + r)] = u[b][r];
         }
     }
-    __syncthreads();
-    fft_tail_tab<C, LOGN, NSEQ, NT, INV>(buf, sstr, tab, tid);
+    sync();
+    fft_tail_tab<C, LOGN, NSEQ, NT, INV>(buf, sstr, tab, tid, sync);
 }
 
 // Full in-place FFT of NSEQ sequences of 2^LOGN points in shared memory

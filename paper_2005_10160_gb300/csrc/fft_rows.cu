@@ -20,8 +20,8 @@ namespace grav {
 
 namespace {
 
-template <typename R, int LOGP, int NSEQ, int NT>
-__global__ void __launch_bounds__(NT) row_r2c_kernel(const R* __restrict__ in, size_t in_ostride, size_t in_istride,
+template <typename R, int LOGP, int NSEQ, int NT, bool VEC>
+__global__ void __launch_bounds__(NT, 2) row_r2c_kernel(const R* __restrict__ in, size_t in_ostride, size_t in_istride,
                                                       int l_in, int I, int O,
                                                       typename cplx<R>::type* __restrict__ out, int i_pad,
                                                       const typename cplx<R>::type* __restrict__ tw, int tw_shift) {
@@ -35,15 +35,52 @@ __global__ void __launch_bounds__(NT) row_r2c_kernel(const R* __restrict__ in, s
     const int i_base = blockIdx.x * (2 * NSEQ);
     const R* in_o = in + (size_t)o * in_ostride;
 
-    for (int e = tid; e < NSEQ * P; e += NT) {
-        const int s = e / P, x = e - s * P;
-        const int i0 = i_base + 2 * s, i1 = i0 + 1;
-        R a = 0, b = 0;
-        if (x < l_in) {
-            if (i0 < I) a = in_o[(size_t)i0 * in_istride + x];
-            if (i1 < I) b = in_o[(size_t)i1 * in_istride + x];
+    if constexpr (VEC) {
+        // Rows of at most P/2 values, a multiple of 4, 16-byte aligned: all
+        // of this thread's vector loads are issued before any is used.
+        static_assert(sizeof(R) == 4, "vector path is for float rows");
+        constexpr int KMAX = (NSEQ * (P / 2) / 4 + NT - 1) / NT;
+        const int nvec = l_in >> 2;
+        float4 va[KMAX], vb[KMAX];
+#pragma unroll
+        for (int k = 0; k < KMAX; ++k) {
+            const int e = tid + k * NT;
+            va[k] = vb[k] = make_float4(0.f, 0.f, 0.f, 0.f);
+            if (e < NSEQ * nvec) {
+                const int s = e / nvec, xv = e - s * nvec;
+                const int i0 = i_base + 2 * s, i1 = i0 + 1;
+                if (i0 < I) va[k] = __ldg(reinterpret_cast<const float4*>(in_o + (size_t)i0 * in_istride) + xv);
+                if (i1 < I) vb[k] = __ldg(reinterpret_cast<const float4*>(in_o + (size_t)i1 * in_istride) + xv);
+            }
         }
-        buf[s * SSTR + sidx<C>(x)] = cmk<C>(a, b);
+#pragma unroll
+        for (int k = 0; k < KMAX; ++k) {
+            const int e = tid + k * NT;
+            if (e < NSEQ * nvec) {
+                const int s = e / nvec, x = 4 * (e - s * nvec);
+                C* d = buf + s * SSTR;
+                d[sidx<C>(x + 0)] = cmk<C>(va[k].x, vb[k].x);
+                d[sidx<C>(x + 1)] = cmk<C>(va[k].y, vb[k].y);
+                d[sidx<C>(x + 2)] = cmk<C>(va[k].z, vb[k].z);
+                d[sidx<C>(x + 3)] = cmk<C>(va[k].w, vb[k].w);
+            }
+        }
+        const int pad = P - 4 * nvec;
+        for (int e = tid; e < NSEQ * pad; e += NT) {
+            const int s = e / pad, x = 4 * nvec + (e - s * pad);
+            buf[s * SSTR + sidx<C>(x)] = cmk<C>(0, 0);
+        }
+    } else {
+        for (int e = tid; e < NSEQ * P; e += NT) {
+            const int s = e / P, x = e - s * P;
+            const int i0 = i_base + 2 * s, i1 = i0 + 1;
+            R a = 0, b = 0;
+            if (x < l_in) {
+                if (i0 < I) a = in_o[(size_t)i0 * in_istride + x];
+                if (i1 < I) b = in_o[(size_t)i1 * in_istride + x];
+            }
+            buf[s * SSTR + sidx<C>(x)] = cmk<C>(a, b);
+        }
     }
     __syncthreads();
     block_fft<C, LOGP, NSEQ, NT, false>(buf, SSTR, tw, tw_shift, tid);
@@ -60,13 +97,17 @@ __global__ void __launch_bounds__(NT) row_r2c_kernel(const R* __restrict__ in, s
         const C d = csub(zk, zm);
         const C B = cmk<C>(half * d.y, -half * d.x);
         C* dst = out + ((size_t)kx * O + o) * i_pad + i0;
-        dst[0] = A;
-        if (i1 < I) dst[1] = B;
+        if (VEC && i1 < I) {
+            *reinterpret_cast<float4*>(dst) = make_float4(A.x, A.y, B.x, B.y);
+        } else {
+            dst[0] = A;
+            if (i1 < I) dst[1] = B;
+        }
     }
 }
 
 template <typename R, int LOGP, int NSEQ, int NT>
-__global__ void __launch_bounds__(NT) row_c2r_kernel(const typename cplx<R>::type* __restrict__ in0,
+__global__ void __launch_bounds__(NT, 2) row_c2r_kernel(const typename cplx<R>::type* __restrict__ in0,
                                                       const typename cplx<R>::type* __restrict__ in1, int I, int O,
                                                       int i_pad, R* __restrict__ out, size_t out_stride, int l_out,
                                                       const typename cplx<R>::type* __restrict__ tw, int tw_shift) {
@@ -118,14 +159,14 @@ template <typename R> constexpr int nseq_for(int logp) {
     return n < 1 ? 1 : (n > 8 ? 8 : n);
 }
 
-template <typename R, int LOGP>
-cudaError_t r2c_impl(const R* in, size_t in_ostride, size_t in_istride, int l_in, int I, int O, void* out, int i_pad,
-                     const void* tw, int log_t, cudaStream_t s) {
+template <typename R, int LOGP, bool VEC>
+cudaError_t r2c_launch(const R* in, size_t in_ostride, size_t in_istride, int l_in, int I, int O, void* out, int i_pad,
+                       const void* tw, int log_t, cudaStream_t s) {
     using C = typename cplx<R>::type;
     constexpr int NSEQ = nseq_for<R>(LOGP);
-    constexpr int NT = 256;
+    constexpr int NT = 512;
     const size_t smem = (size_t)NSEQ * spad_len<C>(1 << LOGP) * sizeof(C);
-    auto k = row_r2c_kernel<R, LOGP, NSEQ, NT>;
+    auto k = row_r2c_kernel<R, LOGP, NSEQ, NT, VEC>;
     cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     dim3 grid((I + 2 * NSEQ - 1) / (2 * NSEQ), O);
@@ -134,11 +175,23 @@ cudaError_t r2c_impl(const R* in, size_t in_ostride, size_t in_istride, int l_in
 }
 
 template <typename R, int LOGP>
+cudaError_t r2c_impl(const R* in, size_t in_ostride, size_t in_istride, int l_in, int I, int O, void* out, int i_pad,
+                     const void* tw, int log_t, cudaStream_t s) {
+    // float rows of at most P/2 values, whole 16-byte vectors, aligned
+    if constexpr (sizeof(R) == 4) {
+        const bool vec = l_in <= (1 << LOGP) / 2 && l_in % 4 == 0 && in_istride % 4 == 0 && in_ostride % 4 == 0 &&
+                         (reinterpret_cast<uintptr_t>(in) & 15) == 0 && i_pad % 2 == 0;
+        if (vec) return r2c_launch<R, LOGP, true>(in, in_ostride, in_istride, l_in, I, O, out, i_pad, tw, log_t, s);
+    }
+    return r2c_launch<R, LOGP, false>(in, in_ostride, in_istride, l_in, I, O, out, i_pad, tw, log_t, s);
+}
+
+template <typename R, int LOGP>
 cudaError_t c2r_impl(const void* in0, const void* in1, int I, int O, int i_pad, R* out, size_t out_stride, int l_out,
                      const void* tw, int log_t, cudaStream_t s) {
     using C = typename cplx<R>::type;
     constexpr int NSEQ = nseq_for<R>(LOGP);
-    constexpr int NT = 256;
+    constexpr int NT = 512;
     const size_t smem = (size_t)NSEQ * spad_len<C>(1 << LOGP) * sizeof(C);
     auto k = row_c2r_kernel<R, LOGP, NSEQ, NT>;
     cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);

@@ -82,7 +82,10 @@ template <typename R> struct FwdCfg {
 // Forward column stage, one CTA per (kx, r) with blockIdx.x = 2 kx + r (the
 // two parities of a column run side by side and share its row transforms
 // through L2).  Thread q owns mirror pair q and accumulates every component
-// for both of its bins; thread 0 also issues the bulk copies.
+// for both of its bins; thread 0 also issues the bulk copies.  When each
+// layer of a round has at least a warp of threads, the NSEQ layers are
+// transformed by separate warp groups that synchronise on their own named
+// barriers, so only three block-wide barriers remain per round.
 //
 // The per-layer product is S v with S = s or i s (imaginary spectra) and,
 // for the mirror bin, S = +-s (odd components).  Both factors are constant
@@ -91,13 +94,15 @@ template <typename R> struct FwdCfg {
 // The layer sum is compensated per round of NSEQ layers: the round's terms
 // are added in plain arithmetic and the round total enters a Kahan sum.
 template <typename R, int LOGN, int NC>
-__global__ void __launch_bounds__(ColShape<LOGN>::J, 1)
+__global__ void __launch_bounds__(ColShape<LOGN>::J, ColShape<LOGN>::J <= 256 ? 2 : 1)
     forward_column_kernel(ColumnArgs a, FwdSmem L, const typename cplx<R>::type* __restrict__ X,
                           const R* __restrict__ spec, typename cplx<R>::type* __restrict__ Y,
                           const typename cplx<R>::type* __restrict__ tw, int* __restrict__ err) {
     using C = typename cplx<R>::type;
     constexpr int N = 1 << LOGN, J = ColShape<LOGN>::J, NT = J;
     constexpr int NSEQ = FwdCfg<R>::NSEQ;
+    constexpr int NTG = NT / NSEQ;  // threads per layer group
+    constexpr bool GROUPED = NTG >= 32 && NTG % 32 == 0;
     constexpr bool KAHAN = sizeof(R) == 4;
     constexpr int SSTR = spad_len<C>(N);
     extern __shared__ __align__(128) unsigned char smem[];
@@ -107,15 +112,16 @@ __global__ void __launch_bounds__(ColShape<LOGN>::J, 1)
     C* ttab = tws + N;                                  // per-pass FFT twiddles
 
     const int tid = threadIdx.x;
+    const int grp = tid / NTG, lt = tid - grp * NTG;
     const int r = blockIdx.x & 1, kx = blockIdx.x >> 1;
-    const int nz = a.nz, ny = a.ny;
+    const int nz = a.nz, ny = a.ny, depth = L.depth;
     const C* Xk = X + (size_t)kx * nz * a.ny_pad;
     const size_t s_row = (size_t)a.ncomp * a.jp;
     const R* Sk = spec + (size_t)(r * a.kx_count + kx) * nz * s_row;
     auto stage_x = [&](int s) { return reinterpret_cast<const C*>(smem + (size_t)s * L.stage_bytes); };
     auto stage_s = [&](int s) { return reinterpret_cast<const R*>(smem + (size_t)s * L.stage_bytes + L.x_bytes); };
     auto issue = [&](int n) {
-        const int s = n % L.depth;
+        const int s = n % depth;
         unsigned char* dst = smem + (size_t)s * L.stage_bytes;
         mbar_arrive_expect_tx(&bars[s], L.x_bytes + L.s_bytes);
         bulk_g2s(dst, Xk + (size_t)n * a.ny_pad, L.x_bytes, &bars[s]);
@@ -123,13 +129,13 @@ __global__ void __launch_bounds__(ColShape<LOGN>::J, 1)
     };
 
     if (tid == 0) {
-        for (int s = 0; s < L.depth; ++s) mbar_init(&bars[s], 1);
+        for (int s = 0; s < depth; ++s) mbar_init(&bars[s], 1);
         fence_mbar_init();
     }
     for (int e = tid; e < N; e += NT) tws[e] = tw[e << a.tw_shift_p];
     build_tw_tab<C, LOGN, NT>(ttab, tw, a.tw_shift_n, tid);
     __syncthreads();
-    const int first = nz < L.depth ? nz : L.depth;
+    const int first = nz < depth ? nz : depth;
     if (tid == 0)
         for (int n = 0; n < first; ++n) issue(n);
 
@@ -145,43 +151,63 @@ __global__ void __launch_bounds__(ColShape<LOGN>::J, 1)
 
     for (int n0 = 0; n0 < nz; n0 += NSEQ) {
         const int cnt = nz - n0 < NSEQ ? nz - n0 : NSEQ;
+        int st[NSEQ];
+#pragma unroll
+        for (int l = 0; l < NSEQ; ++l) st[l] = (n0 + l) % depth;
         bool ok = true;
-        for (int l = 0; l < cnt; ++l) {
-            const int n = n0 + l;
-            ok = ok && mbar_wait_bounded(&bars[n % L.depth], (uint32_t)((n / L.depth) & 1), kWaitLimitNs);
-        }
+        for (int l = 0; l < cnt; ++l)
+            ok = ok && mbar_wait_bounded(&bars[st[l]], (uint32_t)(((n0 + l) / depth) & 1), kWaitLimitNs);
         if (__syncthreads_or(!ok)) {
             // A copy never arrived: record it, let the copies still in
             // flight land (bounded), and leave.
             if (tid == 0) {
                 atomicExch(err, 1);
-                const int last = n0 + L.depth < nz ? n0 + L.depth : nz;
+                const int last = n0 + depth < nz ? n0 + depth : nz;
                 for (int n = n0; n < last; ++n)
-                    mbar_wait_bounded(&bars[n % L.depth], (uint32_t)((n / L.depth) & 1), kWaitLimitNs);
+                    mbar_wait_bounded(&bars[n % depth], (uint32_t)((n / depth) & 1), kWaitLimitNs);
             }
             return;
         }
         // Column FFTs of the round's layers; the first pass reads the staged
         // rows and folds them for ky parity r: a[m] = x[m] W_Py^(m r).
-        block_fft_tab_from<C, LOGN, NSEQ, NT, false>(fbuf, SSTR, ttab, tid, [&](int l, int m) {
-            C v = cmk<C>(0, 0);
-            if (l < cnt && m < ny) {
-                v = stage_x((n0 + l) % L.depth)[m];
-                if (r) v = cmul(v, tws[m]);
+        if constexpr (GROUPED) {
+            if (grp < cnt) {
+                const C* xs = stage_x((n0 + grp) % depth);
+                block_fft_tab_from<C, LOGN, 1, NTG, false>(
+                    fbuf + grp * SSTR, SSTR, ttab, lt,
+                    [&](int, int m) {
+                        C v = cmk<C>(0, 0);
+                        if (m < ny) {
+                            v = xs[m];
+                            if (r) v = cmul(v, tws[m]);
+                        }
+                        return v;
+                    },
+                    GroupSync{1 + grp, NTG});
             }
-            return v;
-        });
+            __syncthreads();
+        } else {
+            block_fft_tab_from<C, LOGN, NSEQ, NT, false>(fbuf, SSTR, ttab, tid, [&](int l, int m) {
+                C v = cmk<C>(0, 0);
+                if (l < cnt && m < ny) {
+                    v = stage_x(st[l])[m];
+                    if (r) v = cmul(v, tws[m]);
+                }
+                return v;
+            });
+        }
         R part[NC][4];
 #pragma unroll
         for (int c = 0; c < NC; ++c)
 #pragma unroll
             for (int j = 0; j < 4; ++j) part[c][j] = 0;
-        for (int l = 0; l < cnt; ++l) {
-            const C v1 = fbuf[l * SSTR + sidx<C>(k1)], v2 = fbuf[l * SSTR + sidx<C>(k2)];
-            const R* Ss = stage_s((n0 + l) % L.depth) + q;
 #pragma unroll
-            for (int c = 0; c < NC; ++c) {
-                if (c < a.ncomp) {
+        for (int l = 0; l < NSEQ; ++l) {
+            if (l < cnt) {
+                const C v1 = fbuf[l * SSTR + sidx<C>(k1)], v2 = fbuf[l * SSTR + sidx<C>(k2)];
+                const R* Ss = stage_s(st[l]) + q;
+#pragma unroll
+                for (int c = 0; c < NC; ++c) {
                     const R s1 = Ss[c * a.jp];
                     const R s2 = nyq ? Ss[c * a.jp + J] : s1;
                     part[c][0] += s1 * v1.x;
@@ -202,7 +228,7 @@ __global__ void __launch_bounds__(ColShape<LOGN>::J, 1)
         if (tid == 0) {
             fence_proxy_async_smem();
             for (int l = 0; l < cnt; ++l)
-                if (n0 + l + L.depth < nz) issue(n0 + l + L.depth);
+                if (n0 + l + depth < nz) issue(n0 + l + depth);
         }
     }
 
@@ -230,14 +256,28 @@ __global__ void __launch_bounds__(ColShape<LOGN>::J, 1)
             }
         }
         __syncthreads();
-        block_fft_tab<C, LOGN, NSEQ, NT, true>(fbuf, SSTR, ttab, tid);
-        for (int e = tid; e < NSEQ * ny; e += NT) {
-            const int l = e / ny, y = e - l * ny;
-            const int c = c0 + l;
-            if (c < a.ncomp) {
-                C v = fbuf[l * SSTR + sidx<C>(y)];
-                if (r) v = cmul(v, cconj(tws[y]));
-                Y[((size_t)(r * a.kx_count + kx) * a.ncomp + c) * a.ny_pad + y] = v;
+        if constexpr (GROUPED) {
+            const int c = c0 + grp;
+            if (c < NC) {
+                C* fb = fbuf + grp * SSTR;
+                block_fft_tab<C, LOGN, 1, NTG, true>(fb, SSTR, ttab, lt, GroupSync{1 + grp, NTG});
+                C* dst = Y + ((size_t)(r * a.kx_count + kx) * a.ncomp + c) * a.ny_pad;
+                for (int y = lt; y < ny; y += NTG) {
+                    C v = fb[sidx<C>(y)];
+                    if (r) v = cmul(v, cconj(tws[y]));
+                    dst[y] = v;
+                }
+            }
+        } else {
+            block_fft_tab<C, LOGN, NSEQ, NT, true>(fbuf, SSTR, ttab, tid);
+            for (int e = tid; e < NSEQ * ny; e += NT) {
+                const int l = e / ny, y = e - l * ny;
+                const int c = c0 + l;
+                if (c < NC) {
+                    C v = fbuf[l * SSTR + sidx<C>(y)];
+                    if (r) v = cmul(v, cconj(tws[y]));
+                    Y[((size_t)(r * a.kx_count + kx) * a.ncomp + c) * a.ny_pad + y] = v;
+                }
             }
         }
         __syncthreads();
@@ -395,7 +435,7 @@ FwdSmem forward_smem(int log_n, int ny_pad, int ncomp, int jp, int max_bytes) {
 
 inline int cpg_for(int ncomp) { return (ncomp + 1) / 2; }
 
-// Components per thread instantiated for the forward kernel.
-inline int nc_for(int ncomp) { return ncomp == 5 ? 6 : ncomp; }
+// Components per thread instantiated for the forward kernel (exactly ncomp).
+inline int nc_for(int ncomp) { return ncomp; }
 
 }  // namespace grav

@@ -26,6 +26,7 @@ cudaError_t forward_impl(const ColumnArgs& a, const void* X, const R* spec, void
         case 2: return forward_impl<R, L, 2>(a, in, spec, out, tw, err, s);      \
         case 3: return forward_impl<R, L, 3>(a, in, spec, out, tw, err, s);      \
         case 4: return forward_impl<R, L, 4>(a, in, spec, out, tw, err, s);      \
+        case 5: return forward_impl<R, L, 5>(a, in, spec, out, tw, err, s);      \
         case 6: return forward_impl<R, L, 6>(a, in, spec, out, tw, err, s);      \
         default: return forward_impl<R, L, 7>(a, in, spec, out, tw, err, s);     \
     }
