@@ -33,13 +33,23 @@ template <typename C, bool INV> __device__ __forceinline__ C cmul_ni(C a) {
     return INV ? cmk<C>(-a.y, a.x) : cmk<C>(a.y, -a.x);
 }
 
-// Padded shared-memory index: one spare slot per 128 bytes keeps the
-// strided Stockham stores at (or near) the minimum number of wavefronts.
-template <typename C> __device__ __forceinline__ int sidx(int e) {
-    return e + (e >> (sizeof(C) == 8 ? 4 : 3));
+// Padded shared-memory index: 16 spare bytes per 128 (8-byte elements: two
+// per 16, which keeps even indices 16-byte aligned; 16-byte elements: one
+// per 8) keep the strided Stockham stores at (or near) the minimum number
+// of wavefronts.
+template <typename C> __host__ __device__ __forceinline__ constexpr int sidx(int e) {
+    return sizeof(C) == 8 ? e + 2 * (e >> 4) : e + (e >> 3);
 }
 template <typename C> __host__ __device__ constexpr int spad_len(int n) {
-    return n + (n >> (sizeof(C) == 8 ? 4 : 3)) + 1;
+    return sizeof(C) == 8 ? n + 2 * (n >> 4) + 2 : n + (n >> 3) + 1;
+}
+
+// Stride between sequences that sit back to back: the padded length rounded
+// so that the same element of consecutive sequences falls in different
+// banks (8-byte elements: stride = 4 mod 16; 16-byte elements: 2 mod 8).
+template <typename C> __host__ __device__ constexpr int seq_stride(int n) {
+    const int len = spad_len<C>(n);
+    return sizeof(C) == 8 ? len + ((4 - len % 16) + 16) % 16 : len + ((2 - len % 8) + 8) % 8;
 }
 
 // In-register DFTs of size 2, 4, 8.
@@ -74,6 +84,23 @@ template <typename C, int R, bool INV> __device__ __forceinline__ void dftR(C* u
     else dft8<C, INV>(u);
 }
 
+// Twiddles w^1 .. w^(R-1) of a butterfly from w = W^k alone: powers by
+// products of depth <= 3 (w2 = w w, w3 = w2 w, w4 = w2 w2, w5 = w4 w,
+// w6 = w3 w3, w7 = w4 w3), so each costs at most a few roundings.
+template <typename C, int R> __device__ __forceinline__ void twiddle_powers(C w, C* p) {
+    p[1] = w;
+    if constexpr (R >= 4) {
+        p[2] = cmul(w, w);
+        p[3] = cmul(p[2], w);
+    }
+    if constexpr (R >= 8) {
+        p[4] = cmul(p[2], p[2]);
+        p[5] = cmul(p[4], w);
+        p[6] = cmul(p[3], p[3]);
+        p[7] = cmul(p[4], p[3]);
+    }
+}
+
 // Radix of pass p for a 2^LOGN transform: the first pass takes LOGN mod 3
 // (radix 2 or 4), the rest are radix 8.
 __host__ __device__ constexpr int pass_radix(int logn, int p) {
@@ -94,12 +121,15 @@ __host__ __device__ constexpr int pass_ls(int logn, int p) {
 // tid < NT take butterflies tid, tid + NT, ... and hold them in registers
 // across the barrier, so one buffer suffices.  Every thread of the block
 // calls this (it contains __syncthreads()).
-template <typename C, int LOGN, int R, int NSEQ, int NT, bool INV>
-__device__ __forceinline__ void fft_pass(C* buf, int sstr, int ls, const C* __restrict__ tw, int tw_shift, int tid) {
+template <typename C, int LOGN, int P, int NSEQ, int NT, bool INV>
+__device__ __forceinline__ void fft_pass(C* buf, int sstr, const C* __restrict__ tw, int tw_shift, int tid) {
     constexpr int N = 1 << LOGN;
+    constexpr int R = pass_radix(LOGN, P);
+    constexpr int LS = pass_ls(LOGN, P);
     constexpr int NR = N / R;
     constexpr int TOTAL = NSEQ * NR;
     constexpr int BPT = (TOTAL + NT - 1) / NT;
+    constexpr bool LIN_LD = NR % 16 == 0, LIN_ST = LS % 16 == 0 || LS == 1;
     C u[BPT][R];
 #pragma unroll
     for (int b = 0; b < BPT; ++b) {
@@ -107,8 +137,14 @@ __device__ __forceinline__ void fft_pass(C* buf, int sstr, int ls, const C* __re
         if (tid < NT && g < TOTAL) {
             const int s = g / NR, i = g - s * NR;
             const C* x = buf + s * sstr;
+            if constexpr (LIN_LD) {
+                const C* xb = x + sidx<C>(i);
 #pragma unroll
-            for (int r = 0; r < R; ++r) u[b][r] = x[sidx<C>(i + r * NR)];
+                for (int r = 0; r < R; ++r) u[b][r] = xb[r * sidx<C>(NR)];
+            } else {
+#pragma unroll
+                for (int r = 0; r < R; ++r) u[b][r] = x[sidx<C>(i + r * NR)];
+            }
         }
     }
     __syncthreads();
@@ -117,22 +153,28 @@ __device__ __forceinline__ void fft_pass(C* buf, int sstr, int ls, const C* __re
         const int g = tid + b * NT;
         if (tid < NT && g < TOTAL) {
             const int s = g / NR, i = g - s * NR;
-            const int k = i & (ls - 1);
-            if (ls > 1) {
-                // twiddle W_{ls R}^{r k} = W_N^{r k N / (ls R)}
-                const int step = (k * (N / (ls * R))) << tw_shift;
+            const int k = i & (LS - 1);
+            if constexpr (LS > 1) {
+                // twiddles W_{LS R}^{r k} = (W_N^{k N / (LS R)})^r
+                C w = tw[(k * (N / (LS * R))) << tw_shift];
+                if (INV) w.y = -w.y;
+                C pw[R];
+                twiddle_powers<C, R>(w, pw);
 #pragma unroll
-                for (int r = 1; r < R; ++r) {
-                    C w = tw[r * step];
-                    if (INV) w.y = -w.y;
-                    u[b][r] = cmul(u[b][r], w);
-                }
+                for (int r = 1; r < R; ++r) u[b][r] = cmul(u[b][r], pw[r]);
             }
             dftR<C, R, INV>(u[b]);
             C* y = buf + s * sstr;
             const int j = (i - k) * R + k;
+            if constexpr (LIN_ST) {
+                // LS == 1: the R outputs are contiguous inside one pad group
+                C* yb = y + sidx<C>(j);
 #pragma unroll
-            for (int r = 0; r < R; ++r) y[sidx<C>(j + r * ls)] = u[b][r];
+                for (int r = 0; r < R; ++r) yb[LS == 1 ? r : r * sidx<C>(LS)] = u[b][r];
+            } else {
+#pragma unroll
+                for (int r = 0; r < R; ++r) y[sidx<C>(j + r * LS)] = u[b][r];
+            }
         }
     }
     __syncthreads();
@@ -185,6 +227,9 @@ __device__ __forceinline__ void fft_pass_tab(C* buf, int sstr, const C* tab, int
     constexpr int NR = N / R;
     constexpr int TOTAL = NSEQ * NR;
     constexpr int BPT = (TOTAL + NT - 1) / NT;
+    // padded offsets are linear when the stride is a whole number of pad
+    // groups (16 elements): sidx(e + r S) = sidx(e) + r sidx(S)
+    constexpr bool LIN_LD = NR % 16 == 0, LIN_ST = LS % 16 == 0;
     C u[BPT][R];
 #pragma unroll
     for (int b = 0; b < BPT; ++b) {
@@ -192,8 +237,14 @@ __device__ __forceinline__ void fft_pass_tab(C* buf, int sstr, const C* tab, int
         if (tid < NT && g < TOTAL) {
             const int s = g / NR, i = g - s * NR;
             const C* x = buf + s * sstr;
+            if constexpr (LIN_LD) {
+                const C* xb = x + sidx<C>(i);
 #pragma unroll
-            for (int r = 0; r < R; ++r) u[b][r] = x[sidx<C>(i + r * NR)];
+                for (int r = 0; r < R; ++r) u[b][r] = xb[r * sidx<C>(NR)];
+            } else {
+#pragma unroll
+                for (int r = 0; r < R; ++r) u[b][r] = x[sidx<C>(i + r * NR)];
+            }
         }
     }
     sync();
@@ -203,17 +254,24 @@ __device__ __forceinline__ void fft_pass_tab(C* buf, int sstr, const C* tab, int
         if (tid < NT && g < TOTAL) {
             const int s = g / NR, i = g - s * NR;
             const int k = i & (LS - 1);
+            const C* t = tab + OFF + k;
 #pragma unroll
             for (int r = 1; r < R; ++r) {
-                C w = tab[OFF + (r - 1) * LS + k];
+                C w = t[(r - 1) * LS];
                 if (INV) w.y = -w.y;
                 u[b][r] = cmul(u[b][r], w);
             }
             dftR<C, R, INV>(u[b]);
             C* y = buf + s * sstr;
             const int j = (i - k) * R + k;
+            if constexpr (LIN_ST) {
+                C* yb = y + sidx<C>(j);
 #pragma unroll
-            for (int r = 0; r < R; ++r) y[sidx<C>(j + r * LS)] = u[b][r];
+                for (int r = 0; r < R; ++r) yb[r * sidx<C>(LS)] = u[b][r];
+            } else {
+#pragma unroll
+                for (int r = 0; r < R; ++r) y[sidx<C>(j + r * LS)] = u[b][r];
+            }
         }
     }
     sync();
@@ -245,9 +303,9 @@ __device__ __forceinline__ void fft_first_pass_from(C* buf, int sstr, int tid, L
 #pragma unroll
             for (int r = 0; r < R; ++r) u[r] = load(s, i + r * NR);
             dftR<C, R, INV>(u);
-            C* y = buf + s * sstr;
+            C* yb = buf + s * sstr + sidx<C>(i * R);  // R <= 8 outputs inside one pad group
 #pragma unroll
-            for (int r = 0; r < R; ++r) y[sidx<C>(i * R + r)] = u[r];
+            for (int r = 0; r < R; ++r) yb[r] = u[r];
         }
     }
     sync();
@@ -261,10 +319,10 @@ __device__ __forceinline__ void block_fft_from(C* buf, int sstr, const C* __rest
     constexpr int NP = num_passes(LOGN);
     static_assert(NP <= 5, "transform too long");
     fft_first_pass_from<C, LOGN, pass_radix(LOGN, 0), NSEQ, NT, INV>(buf, sstr, tid, load);
-    if constexpr (NP > 1) fft_pass<C, LOGN, pass_radix(LOGN, 1), NSEQ, NT, INV>(buf, sstr, pass_ls(LOGN, 1), tw, tw_shift, tid);
-    if constexpr (NP > 2) fft_pass<C, LOGN, pass_radix(LOGN, 2), NSEQ, NT, INV>(buf, sstr, pass_ls(LOGN, 2), tw, tw_shift, tid);
-    if constexpr (NP > 3) fft_pass<C, LOGN, pass_radix(LOGN, 3), NSEQ, NT, INV>(buf, sstr, pass_ls(LOGN, 3), tw, tw_shift, tid);
-    if constexpr (NP > 4) fft_pass<C, LOGN, pass_radix(LOGN, 4), NSEQ, NT, INV>(buf, sstr, pass_ls(LOGN, 4), tw, tw_shift, tid);
+    if constexpr (NP > 1) fft_pass<C, LOGN, 1, NSEQ, NT, INV>(buf, sstr, tw, tw_shift, tid);
+    if constexpr (NP > 2) fft_pass<C, LOGN, 2, NSEQ, NT, INV>(buf, sstr, tw, tw_shift, tid);
+    if constexpr (NP > 3) fft_pass<C, LOGN, 3, NSEQ, NT, INV>(buf, sstr, tw, tw_shift, tid);
+    if constexpr (NP > 4) fft_pass<C, LOGN, 4, NSEQ, NT, INV>(buf, sstr, tw, tw_shift, tid);
 }
 
 // The same with table twiddles: inputs from load(s, m), result in buf.
@@ -301,8 +359,9 @@ __device__ __forceinline__ void block_fft_tab(C* buf, int sstr, const C* tab, in
         if (tid < NT && g < TOTAL) {
             const int s = g / NR, i = g - s * NR;
             dftR<C, R, INV>(u[b]);
+            C* yb = buf + s * sstr + sidx<C>(i * R);
 #pragma unroll
-            for (int r = 0; r < R; ++r) buf[s * sstr + sidx<C>(i * R + r)] = u[b][r];
+            for (int r = 0; r < R; ++r) yb[r] = u[b][r];
         }
     }
     sync();
@@ -315,11 +374,11 @@ template <typename C, int LOGN, int NSEQ, int NT, bool INV>
 __device__ __forceinline__ void block_fft(C* buf, int sstr, const C* __restrict__ tw, int tw_shift, int tid) {
     constexpr int NP = num_passes(LOGN);
     static_assert(NP <= 5, "transform too long");
-    if constexpr (NP > 0) fft_pass<C, LOGN, pass_radix(LOGN, 0), NSEQ, NT, INV>(buf, sstr, pass_ls(LOGN, 0), tw, tw_shift, tid);
-    if constexpr (NP > 1) fft_pass<C, LOGN, pass_radix(LOGN, 1), NSEQ, NT, INV>(buf, sstr, pass_ls(LOGN, 1), tw, tw_shift, tid);
-    if constexpr (NP > 2) fft_pass<C, LOGN, pass_radix(LOGN, 2), NSEQ, NT, INV>(buf, sstr, pass_ls(LOGN, 2), tw, tw_shift, tid);
-    if constexpr (NP > 3) fft_pass<C, LOGN, pass_radix(LOGN, 3), NSEQ, NT, INV>(buf, sstr, pass_ls(LOGN, 3), tw, tw_shift, tid);
-    if constexpr (NP > 4) fft_pass<C, LOGN, pass_radix(LOGN, 4), NSEQ, NT, INV>(buf, sstr, pass_ls(LOGN, 4), tw, tw_shift, tid);
+    if constexpr (NP > 0) fft_pass<C, LOGN, 0, NSEQ, NT, INV>(buf, sstr, tw, tw_shift, tid);
+    if constexpr (NP > 1) fft_pass<C, LOGN, 1, NSEQ, NT, INV>(buf, sstr, tw, tw_shift, tid);
+    if constexpr (NP > 2) fft_pass<C, LOGN, 2, NSEQ, NT, INV>(buf, sstr, tw, tw_shift, tid);
+    if constexpr (NP > 3) fft_pass<C, LOGN, 3, NSEQ, NT, INV>(buf, sstr, tw, tw_shift, tid);
+    if constexpr (NP > 4) fft_pass<C, LOGN, 4, NSEQ, NT, INV>(buf, sstr, tw, tw_shift, tid);
 }
 
 }  // namespace grav

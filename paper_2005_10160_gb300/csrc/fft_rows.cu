@@ -27,7 +27,7 @@ __global__ void __launch_bounds__(NT, 2) row_r2c_kernel(const R* __restrict__ in
                                                       const typename cplx<R>::type* __restrict__ tw, int tw_shift) {
     using C = typename cplx<R>::type;
     constexpr int P = 1 << LOGP;
-    constexpr int SSTR = spad_len<C>(P);
+    constexpr int SSTR = seq_stride<C>(P);
     extern __shared__ __align__(16) unsigned char smem_raw[];
     C* buf = reinterpret_cast<C*>(smem_raw);
     const int tid = threadIdx.x;
@@ -36,38 +36,36 @@ __global__ void __launch_bounds__(NT, 2) row_r2c_kernel(const R* __restrict__ in
     const R* in_o = in + (size_t)o * in_ostride;
 
     if constexpr (VEC) {
-        // Rows of at most P/2 values, a multiple of 4, 16-byte aligned: all
-        // of this thread's vector loads are issued before any is used.
+        // Rows of at most P/2 values, an even number, 8-byte aligned: every
+        // thread loads element pairs (x, x+1) of both rows with all its loads
+        // issued before any is used, and stores the two complex values with
+        // one 16-byte shared store.
         static_assert(sizeof(R) == 4, "vector path is for float rows");
-        constexpr int KMAX = (NSEQ * (P / 2) / 4 + NT - 1) / NT;
-        const int nvec = l_in >> 2;
-        float4 va[KMAX], vb[KMAX];
+        constexpr int KMAX = (NSEQ * (P / 2) / 2 + NT - 1) / NT;
+        const int npair = l_in >> 1;
+        float2 va[KMAX], vb[KMAX];
 #pragma unroll
         for (int k = 0; k < KMAX; ++k) {
             const int e = tid + k * NT;
-            va[k] = vb[k] = make_float4(0.f, 0.f, 0.f, 0.f);
-            if (e < NSEQ * nvec) {
-                const int s = e / nvec, xv = e - s * nvec;
+            va[k] = vb[k] = make_float2(0.f, 0.f);
+            if (e < NSEQ * npair) {
+                const int s = e / npair, xp = e - s * npair;
                 const int i0 = i_base + 2 * s, i1 = i0 + 1;
-                if (i0 < I) va[k] = __ldg(reinterpret_cast<const float4*>(in_o + (size_t)i0 * in_istride) + xv);
-                if (i1 < I) vb[k] = __ldg(reinterpret_cast<const float4*>(in_o + (size_t)i1 * in_istride) + xv);
+                if (i0 < I) va[k] = __ldg(reinterpret_cast<const float2*>(in_o + (size_t)i0 * in_istride) + xp);
+                if (i1 < I) vb[k] = __ldg(reinterpret_cast<const float2*>(in_o + (size_t)i1 * in_istride) + xp);
             }
         }
 #pragma unroll
         for (int k = 0; k < KMAX; ++k) {
             const int e = tid + k * NT;
-            if (e < NSEQ * nvec) {
-                const int s = e / nvec, x = 4 * (e - s * nvec);
-                C* d = buf + s * SSTR;
-                d[sidx<C>(x + 0)] = cmk<C>(va[k].x, vb[k].x);
-                d[sidx<C>(x + 1)] = cmk<C>(va[k].y, vb[k].y);
-                d[sidx<C>(x + 2)] = cmk<C>(va[k].z, vb[k].z);
-                d[sidx<C>(x + 3)] = cmk<C>(va[k].w, vb[k].w);
+            if (e < NSEQ * npair) {
+                const int s = e / npair, x = 2 * (e - s * npair);
+                *reinterpret_cast<float4*>(buf + s * SSTR + sidx<C>(x)) = make_float4(va[k].x, vb[k].x, va[k].y, vb[k].y);
             }
         }
-        const int pad = P - 4 * nvec;
+        const int pad = P - 2 * npair;
         for (int e = tid; e < NSEQ * pad; e += NT) {
-            const int s = e / pad, x = 4 * nvec + (e - s * pad);
+            const int s = e / pad, x = 2 * npair + (e - s * pad);
             buf[s * SSTR + sidx<C>(x)] = cmk<C>(0, 0);
         }
     } else {
@@ -113,7 +111,7 @@ __global__ void __launch_bounds__(NT, 2) row_c2r_kernel(const typename cplx<R>::
                                                       const typename cplx<R>::type* __restrict__ tw, int tw_shift) {
     using C = typename cplx<R>::type;
     constexpr int P = 1 << LOGP;
-    constexpr int SSTR = spad_len<C>(P);
+    constexpr int SSTR = seq_stride<C>(P);
     extern __shared__ __align__(16) unsigned char smem_raw[];
     C* buf = reinterpret_cast<C*>(smem_raw);
     const int tid = threadIdx.x;
@@ -165,7 +163,7 @@ cudaError_t r2c_launch(const R* in, size_t in_ostride, size_t in_istride, int l_
     using C = typename cplx<R>::type;
     constexpr int NSEQ = nseq_for<R>(LOGP);
     constexpr int NT = 512;
-    const size_t smem = (size_t)NSEQ * spad_len<C>(1 << LOGP) * sizeof(C);
+    const size_t smem = (size_t)NSEQ * seq_stride<C>(1 << LOGP) * sizeof(C);
     auto k = row_r2c_kernel<R, LOGP, NSEQ, NT, VEC>;
     cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
@@ -179,8 +177,8 @@ cudaError_t r2c_impl(const R* in, size_t in_ostride, size_t in_istride, int l_in
                      const void* tw, int log_t, cudaStream_t s) {
     // float rows of at most P/2 values, whole 16-byte vectors, aligned
     if constexpr (sizeof(R) == 4) {
-        const bool vec = l_in <= (1 << LOGP) / 2 && l_in % 4 == 0 && in_istride % 4 == 0 && in_ostride % 4 == 0 &&
-                         (reinterpret_cast<uintptr_t>(in) & 15) == 0 && i_pad % 2 == 0;
+        const bool vec = l_in <= (1 << LOGP) / 2 && l_in % 2 == 0 && in_istride % 2 == 0 && in_ostride % 2 == 0 &&
+                         (reinterpret_cast<uintptr_t>(in) & 7) == 0 && i_pad % 2 == 0;
         if (vec) return r2c_launch<R, LOGP, true>(in, in_ostride, in_istride, l_in, I, O, out, i_pad, tw, log_t, s);
     }
     return r2c_launch<R, LOGP, false>(in, in_ostride, in_istride, l_in, I, O, out, i_pad, tw, log_t, s);
@@ -192,7 +190,7 @@ cudaError_t c2r_impl(const void* in0, const void* in1, int I, int O, int i_pad, 
     using C = typename cplx<R>::type;
     constexpr int NSEQ = nseq_for<R>(LOGP);
     constexpr int NT = 512;
-    const size_t smem = (size_t)NSEQ * spad_len<C>(1 << LOGP) * sizeof(C);
+    const size_t smem = (size_t)NSEQ * seq_stride<C>(1 << LOGP) * sizeof(C);
     auto k = row_c2r_kernel<R, LOGP, NSEQ, NT>;
     cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;

@@ -201,15 +201,31 @@ __global__ void __launch_bounds__(ColShape<LOGN>::J, ColShape<LOGN>::J <= 256 ? 
         for (int c = 0; c < NC; ++c)
 #pragma unroll
             for (int j = 0; j < 4; ++j) part[c][j] = 0;
+        if (!nyq) {
 #pragma unroll
-        for (int l = 0; l < NSEQ; ++l) {
-            if (l < cnt) {
+            for (int l = 0; l < NSEQ; ++l) {
+                if (l < cnt) {
+                    const C v1 = fbuf[l * SSTR + sidx<C>(k1)], v2 = fbuf[l * SSTR + sidx<C>(k2)];
+                    const R* Ss = stage_s(st[l]) + q;
+#pragma unroll
+                    for (int c = 0; c < NC; ++c) {
+                        const R s1 = Ss[c * a.jp];
+                        part[c][0] += s1 * v1.x;
+                        part[c][1] += s1 * v1.y;
+                        part[c][2] += s1 * v2.x;
+                        part[c][3] += s1 * v2.y;
+                    }
+                }
+            }
+        } else {
+            // pair 0 of the even parity holds ky = 0 and the Nyquist row
+            // ky = Py/2, each with its own stored value
+            for (int l = 0; l < cnt; ++l) {
                 const C v1 = fbuf[l * SSTR + sidx<C>(k1)], v2 = fbuf[l * SSTR + sidx<C>(k2)];
-                const R* Ss = stage_s(st[l]) + q;
+                const R* Ss = stage_s(st[l]);
 #pragma unroll
                 for (int c = 0; c < NC; ++c) {
-                    const R s1 = Ss[c * a.jp];
-                    const R s2 = nyq ? Ss[c * a.jp + J] : s1;
+                    const R s1 = Ss[c * a.jp], s2 = Ss[c * a.jp + J];
                     part[c][0] += s1 * v1.x;
                     part[c][1] += s1 * v1.y;
                     part[c][2] += s2 * v2.x;
@@ -420,7 +436,7 @@ FwdSmem forward_smem(int log_n, int ny_pad, int ncomp, int jp, int max_bytes) {
     L.s_bytes = (uint32_t)(ncomp * jp * sizeof(R));
     L.stage_bytes = (L.x_bytes + L.s_bytes + 127u) & ~127u;
     const uint32_t fft_bytes = (uint32_t)(NSEQ * spad_len<C>(1 << log_n) * sizeof(C));
-    const uint32_t tw_bytes = (uint32_t)(((1u << log_n) + tw_tab_len(log_n)) * sizeof(C));
+    const uint32_t tw_bytes = (uint32_t)(((1u << log_n) + tw_tab_len(log_n)) * sizeof(C));  // fold + pass tables
     int depth = 2 * NSEQ;
     while (depth >= NSEQ && (size_t)depth * L.stage_bytes + fft_bytes + tw_bytes + depth * 8 + 128 > (size_t)max_bytes)
         --depth;
