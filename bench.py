@@ -58,6 +58,9 @@ def parse():
     ap.add_argument("--workload", choices=tuple(WORKLOADS), default="grf1024")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-fp64", action="store_true", help="skip the FP64-spectral comparison leg")
+    ap.add_argument("--serve-requests", type=int, default=1000,
+                    help="requests in the serving leg (Poisson arrivals, 0 to skip)")
+    ap.add_argument("--serve-rate", type=float, default=200.0, help="mean arrival rate of the serving leg (1/s)")
     return ap.parse_args()
 
 
@@ -225,6 +228,58 @@ def cpu_density_sample(mesh, n_layers):
     nx, ny, nz = mesh[:3]
     _, rho = workloads.grf1024(nx, ny, nz, device="cuda" if torch.cuda.is_available() else "cpu")
     return rho[:n_layers].float().cpu().numpy()
+
+
+def serving_leg(n_requests: int, rate: float):
+    """Poisson stream of forward/adjoint requests (50/50) on the four serving
+    meshes (64^2x16, 128^2x32, 256^2x32, 512^2x64 of 20 m cubes, random-box
+    densities, N(0,1) adjoint inputs) through the continuous-batching server;
+    plans are built during a warm-up.  Latency is submission to completion."""
+    import numpy as np
+    import torch
+
+    from paper_2005_10160_gb300 import workloads
+    from paper_2005_10160_gb300.server import Server
+
+    rng = np.random.default_rng(workloads.SEED_BASE + 5)
+    meshes = [workloads.serving_mesh(i) for i in range(4)]
+    pool = {}
+    for i, m in enumerate(meshes):
+        pool[(i, "forward")] = [torch.as_tensor(workloads.serving_density(m, rng), device="cuda") for _ in range(4)]
+        pool[(i, "adjoint")] = [torch.randn((NCOMP, m.ny, m.nx), device="cuda") for _ in range(4)]
+    srv = Server(hbm_budget=48 << 30, slots=4, max_batch=8)
+    try:
+        for i, m in enumerate(meshes):
+            for kind in ("forward", "adjoint"):
+                srv.submit(kind, m, pool[(i, kind)][0])
+        srv.drain()
+        srv.completed.clear()
+        srv.batches_run = srv.graph_replays = 0
+        t0 = time.perf_counter()
+        t_next = t0
+        pairs = 0.0
+        reqs = []
+        for _ in range(n_requests):
+            t_next += float(rng.exponential(1.0 / rate))
+            i = int(rng.integers(4))
+            kind = "forward" if rng.random() < 0.5 else "adjoint"
+            m = meshes[i]
+            delay = t_next - time.perf_counter()
+            if delay > 0:
+                time.sleep(delay)  # sleeping releases the GIL to the server thread
+            reqs.append(srv.submit(kind, m, pool[(i, kind)][int(rng.integers(4))]))
+            pairs += pairs_per_forward(m.tuple())
+        srv.drain()
+        for r in reqs:
+            r.wait(60)
+        st = srv.stats()
+        span = max(r.t_done for r in reqs) - t0
+    finally:
+        srv.close()
+    st.update({"rate_per_s": rate, "pairs_per_s": pairs / span,
+               "workload": "Poisson 50/50 forward/adjoint on 64^2x16, 128^2x32, 256^2x32, 512^2x64 (20 m cubes), "
+                           "FP32 spectra, plans resident"})
+    return st
 
 
 def run_reference(args):
@@ -396,6 +451,11 @@ def run_ours(args):
         plan64.close()
         del rho64, out64
 
+    serving = None
+    if rank == 0 and args.serve_requests > 0:
+        plan.close()
+        serving = serving_leg(args.serve_requests, args.serve_rate)
+
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline and args.workload == "grf1024":
         cores = os.cpu_count() or 1
@@ -416,7 +476,7 @@ def run_ours(args):
                        "parallelism": f"replica x{world}", "plan_create_s": plan_s,
                        "forward_algorithmic_bytes": fwd_alg},
             "roofline": roofline, "clocks": clocks, "e2e": e2e, "gpu_launches": 3 * args.steps,
-            "cpu_baseline": cpu, "fp64_path": fp64,
+            "cpu_baseline": cpu, "fp64_path": fp64, "serving": serving,
         }
         print(json.dumps(line), flush=True)
     plan.close()

@@ -107,6 +107,30 @@ int grav_forward(grav_plan* plan, const void* rho_dev, void* out_dev, void* stre
  * Same types, stream and status codes as grav_forward. */
 int grav_adjoint(grav_plan* plan, const void* r_dev, void* grad_dev, void* stream);
 
+/* Device bytes of scratch one request of a batched call needs (the plan's
+ * own workspaces hold exactly one request).  0 for NULL. */
+size_t grav_workspace_bytes(const grav_plan* plan);
+
+/* Forward of `batch` independent density models on one plan with one launch
+ * per stage (Eq. 21 for each; a serving loop groups requests on the same
+ * mesh this way).
+ *   batch          1 .. 65535
+ *   rho_dev        device [batch][nz][ny][nx]
+ *   out_dev        device [batch][ncomp][ny][nx]
+ *   workspace_dev  device scratch of batch * grav_workspace_bytes(plan) bytes,
+ *                  256-byte aligned, owned by the caller; NULL only for
+ *                  batch == 1 (then the plan's own workspaces are used).
+ *                  Calls with different workspaces may overlap on the GPU.
+ * Returns GRAV_OK, GRAV_EINVAL or GRAV_ECUDA. */
+int grav_forward_batch(grav_plan* plan, int batch, const void* rho_dev, void* out_dev, void* workspace_dev,
+                       void* stream);
+
+/* Adjoint (transpose of Eq. 21) of `batch` data-space vectors:
+ * r_dev [batch][ncomp][ny][nx] -> grad_dev [batch][nz][ny][nx]; workspace as
+ * for grav_forward_batch. */
+int grav_adjoint_batch(grav_plan* plan, int batch, const void* r_dev, void* grad_dev, void* workspace_dev,
+                       void* stream);
+
 /* Release the plan and its device memory (waits for the device first).
  * NULL is ignored. */
 void grav_plan_destroy(grav_plan* plan);

@@ -37,6 +37,9 @@ EXPORTED = (
     "grav_forward_static_scratch",
     "grav_plan_check",
     "grav_selftest_bounded_wait",
+    "grav_workspace_bytes",
+    "grav_forward_batch",
+    "grav_adjoint_batch",
 )
 
 
@@ -96,6 +99,12 @@ def lib() -> ctypes.CDLL:
             L.grav_plan_check.restype = i
             L.grav_selftest_bounded_wait.argtypes = [d, ctypes.POINTER(ctypes.c_double)]
             L.grav_selftest_bounded_wait.restype = i
+            L.grav_workspace_bytes.argtypes = [p]
+            L.grav_workspace_bytes.restype = sz
+            L.grav_forward_batch.argtypes = [p, i, p, p, p, p]
+            L.grav_forward_batch.restype = i
+            L.grav_adjoint_batch.argtypes = [p, i, p, p, p, p]
+            L.grav_adjoint_batch.restype = i
             _lib = L
     return _lib
 
@@ -185,3 +194,15 @@ def grav_selftest_bounded_wait(limit_ms: float):
     waited = ctypes.c_double(0.0)
     rc = lib().grav_selftest_bounded_wait(float(limit_ms), ctypes.byref(waited))
     return rc, waited.value
+
+
+def grav_workspace_bytes(plan) -> int:
+    return int(lib().grav_workspace_bytes(plan))
+
+
+def grav_forward_batch(plan, batch, rho_ptr, out_ptr, ws_ptr, stream=0) -> int:
+    return _check(lib().grav_forward_batch(plan, int(batch), rho_ptr, out_ptr, ws_ptr or None, stream or None))
+
+
+def grav_adjoint_batch(plan, batch, r_ptr, grad_ptr, ws_ptr, stream=0) -> int:
+    return _check(lib().grav_adjoint_batch(plan, int(batch), r_ptr, grad_ptr, ws_ptr or None, stream or None))

@@ -24,6 +24,10 @@ namespace grav {
 namespace {
 thread_local char g_err[512] = "";
 
+template <typename R> struct cplx_of;
+template <> struct cplx_of<float> { using type = float2; };
+template <> struct cplx_of<double> { using type = double2; };
+
 int ilog2(int v) {
     int l = 0;
     while ((1 << l) < v) ++l;
@@ -239,48 +243,86 @@ inline void mark(grav_plan::TimedCall* t, int i, cudaStream_t s) {
     if (t) cudaEventRecord(t->ev[i], s);
 }
 
+// Per-request workspace of a batched call: [A][B], each rounded to 256 bytes.
+size_t ws_a_part(const grav_plan* p) { return round_up(p->ws_a_bytes, 256); }
+size_t ws_req_bytes(const grav_plan* p) { return ws_a_part(p) + round_up(p->ws_b_bytes, 256); }
+
 template <typename R>
-int run_forward(grav_plan* p, const void* rho, void* out, cudaStream_t s) {
+int run_forward(grav_plan* p, const void* rho, void* out, void* wa, void* wb, int batch, size_t ws_stride,
+                cudaStream_t s) {
+    using C = typename cplx_of<R>::type;
+    const size_t cs = ws_stride / sizeof(C);  // workspace stride in complex elements
     cudaError_t e;
-    grav_plan::TimedCall* tc = begin_timed(p, 0);
+    grav_plan::TimedCall* tc = batch == 1 ? begin_timed(p, 0) : nullptr;
     mark(tc, 0, s);
-    e = launch_row_r2c<R>(p->log_px, (const R*)rho, (size_t)p->ny * p->nx, (size_t)p->nx, p->nx, p->ny, p->nz, p->ws_a,
-                          p->ny_pad, p->tw, p->log_t, s);
+    e = launch_row_r2c<R>(p->log_px, (const R*)rho, (size_t)p->ny * p->nx, (size_t)p->nx, p->nx, p->ny, p->nz, wa,
+                          p->ny_pad, p->tw, p->log_t, s, Batch{batch, (size_t)p->nz * p->ny * p->nx, cs});
     if (e != cudaSuccess) return cuda_fail(e, "forward row transform");
     mark(tc, 1, s);
     ColumnArgs a{p->ny, p->ny_pad, p->nz, p->ncomp, p->kx_count, p->jp, p->imag_mask, p->oddv_mask,
                  p->log_t - (p->log_py - 1), p->log_t - p->log_py};
-    e = launch_forward_columns<R>(p->log_py - 1, a, p->ws_a, (const R*)p->spec, p->ws_b, p->tw, p->err_flag, s);
+    e = launch_forward_columns<R>(p->log_py - 1, a, wa, (const R*)p->spec, wb, p->tw, p->err_flag, s,
+                                  Batch{batch, cs, cs});
     if (e != cudaSuccess) return cuda_fail(e, "forward column stage");
     mark(tc, 2, s);
     const size_t half = (size_t)p->kx_count * p->ncomp * p->ny_pad * 2 * sizeof(R);
-    e = launch_row_c2r<R>(p->log_px, p->ws_b, (const unsigned char*)p->ws_b + half, p->ny, p->ncomp, p->ny_pad, (R*)out,
-                          (size_t)p->nx, p->nx, p->tw, p->log_t, s);
+    e = launch_row_c2r<R>(p->log_px, wb, (const unsigned char*)wb + half, p->ny, p->ncomp, p->ny_pad, (R*)out,
+                          (size_t)p->nx, p->nx, p->tw, p->log_t, s,
+                          Batch{batch, cs, (size_t)p->ncomp * p->ny * p->nx});
     if (e != cudaSuccess) return cuda_fail(e, "forward inverse row transform");
     mark(tc, 3, s);
     return GRAV_OK;
 }
 
 template <typename R>
-int run_adjoint(grav_plan* p, const void* r, void* grad, cudaStream_t s) {
+int run_adjoint(grav_plan* p, const void* r, void* grad, void* wa, void* wb, int batch, size_t ws_stride,
+                cudaStream_t s) {
+    using C = typename cplx_of<R>::type;
+    const size_t cs = ws_stride / sizeof(C);
     cudaError_t e;
-    grav_plan::TimedCall* tc = begin_timed(p, 1);
+    grav_plan::TimedCall* tc = batch == 1 ? begin_timed(p, 1) : nullptr;
     mark(tc, 0, s);
-    e = launch_row_r2c<R>(p->log_px, (const R*)r, (size_t)p->ny * p->nx, (size_t)p->nx, p->nx, p->ny, p->ncomp,
-                          p->ws_b, p->ny_pad, p->tw, p->log_t, s);
+    e = launch_row_r2c<R>(p->log_px, (const R*)r, (size_t)p->ny * p->nx, (size_t)p->nx, p->nx, p->ny, p->ncomp, wb,
+                          p->ny_pad, p->tw, p->log_t, s, Batch{batch, (size_t)p->ncomp * p->ny * p->nx, cs});
     if (e != cudaSuccess) return cuda_fail(e, "adjoint row transform");
     mark(tc, 1, s);
     ColumnArgs a{p->ny, p->ny_pad, p->nz, p->ncomp, p->kx_count, p->jp, p->imag_mask, p->oddv_mask,
                  p->log_t - (p->log_py - 1), p->log_t - p->log_py};
-    e = launch_adjoint_columns<R>(p->log_py - 1, a, p->ws_b, (const R*)p->spec, p->ws_a, p->tw, s);
+    e = launch_adjoint_columns<R>(p->log_py - 1, a, wb, (const R*)p->spec, wa, p->tw, p->err_flag, s,
+                                  Batch{batch, cs, cs});
     if (e != cudaSuccess) return cuda_fail(e, "adjoint column stage");
     mark(tc, 2, s);
     const size_t half = (size_t)p->kx_count * p->nz * p->ny_pad * 2 * sizeof(R);
-    e = launch_row_c2r<R>(p->log_px, p->ws_a, (const unsigned char*)p->ws_a + half, p->ny, p->nz, p->ny_pad, (R*)grad,
-                          (size_t)p->nx, p->nx, p->tw, p->log_t, s);
+    e = launch_row_c2r<R>(p->log_px, wa, (const unsigned char*)wa + half, p->ny, p->nz, p->ny_pad, (R*)grad,
+                          (size_t)p->nx, p->nx, p->tw, p->log_t, s, Batch{batch, cs, (size_t)p->nz * p->ny * p->nx});
     if (e != cudaSuccess) return cuda_fail(e, "adjoint inverse row transform");
     mark(tc, 3, s);
     return GRAV_OK;
+}
+
+int batch_call(grav_plan* plan, int batch, const void* in, void* out, void* ws, void* stream, bool adjoint) {
+    const char* name = adjoint ? "grav_adjoint_batch" : "grav_forward_batch";
+    if (!plan || !in || !out || batch < 1 || batch > 65535) {
+        set_error("%s: null plan or buffer, or batch outside 1..65535", name);
+        return GRAV_EINVAL;
+    }
+    if (!ws && batch > 1) {
+        set_error("%s: a batch of %d needs a workspace of %d x grav_workspace_bytes", name, batch, batch);
+        return GRAV_EINVAL;
+    }
+    if (ws && (reinterpret_cast<uintptr_t>(ws) & 255)) {
+        set_error("%s: workspace must be 256-byte aligned", name);
+        return GRAV_EINVAL;
+    }
+    void* wa = ws ? ws : plan->ws_a;
+    void* wb = ws ? (unsigned char*)ws + ws_a_part(plan) : plan->ws_b;
+    const size_t stride = ws_req_bytes(plan);
+    cudaStream_t s = (cudaStream_t)stream;
+    if (adjoint)
+        return plan->fp64 ? run_adjoint<double>(plan, in, out, wa, wb, batch, stride, s)
+                          : run_adjoint<float>(plan, in, out, wa, wb, batch, stride, s);
+    return plan->fp64 ? run_forward<double>(plan, in, out, wa, wb, batch, stride, s)
+                      : run_forward<float>(plan, in, out, wa, wb, batch, stride, s);
 }
 
 }  // namespace
@@ -376,8 +418,7 @@ int grav_forward(grav_plan* plan, const void* rho_dev, void* out_dev, void* stre
         set_error("grav_forward: null plan or buffer");
         return GRAV_EINVAL;
     }
-    cudaStream_t s = (cudaStream_t)stream;
-    return plan->fp64 ? run_forward<double>(plan, rho_dev, out_dev, s) : run_forward<float>(plan, rho_dev, out_dev, s);
+    return batch_call(plan, 1, rho_dev, out_dev, nullptr, stream, false);
 }
 
 int grav_adjoint(grav_plan* plan, const void* r_dev, void* grad_dev, void* stream) {
@@ -385,8 +426,19 @@ int grav_adjoint(grav_plan* plan, const void* r_dev, void* grad_dev, void* strea
         set_error("grav_adjoint: null plan or buffer");
         return GRAV_EINVAL;
     }
-    cudaStream_t s = (cudaStream_t)stream;
-    return plan->fp64 ? run_adjoint<double>(plan, r_dev, grad_dev, s) : run_adjoint<float>(plan, r_dev, grad_dev, s);
+    return batch_call(plan, 1, r_dev, grad_dev, nullptr, stream, true);
+}
+
+size_t grav_workspace_bytes(const grav_plan* plan) { return plan ? ws_req_bytes(plan) : 0; }
+
+int grav_forward_batch(grav_plan* plan, int batch, const void* rho_dev, void* out_dev, void* workspace_dev,
+                       void* stream) {
+    return batch_call(plan, batch, rho_dev, out_dev, workspace_dev, stream, false);
+}
+
+int grav_adjoint_batch(grav_plan* plan, int batch, const void* r_dev, void* grad_dev, void* workspace_dev,
+                       void* stream) {
+    return batch_call(plan, batch, r_dev, grad_dev, workspace_dev, stream, true);
 }
 
 void grav_plan_destroy(grav_plan* plan) {

@@ -24,7 +24,8 @@ template <typename R, int LOGP, int NSEQ, int NT, bool VEC>
 __global__ void __launch_bounds__(NT, 2) row_r2c_kernel(const R* __restrict__ in, size_t in_ostride, size_t in_istride,
                                                       int l_in, int I, int O,
                                                       typename cplx<R>::type* __restrict__ out, int i_pad,
-                                                      const typename cplx<R>::type* __restrict__ tw, int tw_shift) {
+                                                      const typename cplx<R>::type* __restrict__ tw, int tw_shift,
+                                                      size_t in_bstride, size_t out_bstride) {
     using C = typename cplx<R>::type;
     constexpr int P = 1 << LOGP;
     constexpr int SSTR = seq_stride<C>(P);
@@ -33,6 +34,8 @@ __global__ void __launch_bounds__(NT, 2) row_r2c_kernel(const R* __restrict__ in
     const int tid = threadIdx.x;
     const int o = blockIdx.y;
     const int i_base = blockIdx.x * (2 * NSEQ);
+    in += blockIdx.z * in_bstride;
+    out += blockIdx.z * out_bstride;
     const R* in_o = in + (size_t)o * in_ostride;
 
     if constexpr (VEC) {
@@ -108,7 +111,8 @@ template <typename R, int LOGP, int NSEQ, int NT>
 __global__ void __launch_bounds__(NT, 2) row_c2r_kernel(const typename cplx<R>::type* __restrict__ in0,
                                                       const typename cplx<R>::type* __restrict__ in1, int I, int O,
                                                       int i_pad, R* __restrict__ out, size_t out_stride, int l_out,
-                                                      const typename cplx<R>::type* __restrict__ tw, int tw_shift) {
+                                                      const typename cplx<R>::type* __restrict__ tw, int tw_shift,
+                                                      size_t in_bstride, size_t out_bstride) {
     using C = typename cplx<R>::type;
     constexpr int P = 1 << LOGP;
     constexpr int SSTR = seq_stride<C>(P);
@@ -117,6 +121,9 @@ __global__ void __launch_bounds__(NT, 2) row_c2r_kernel(const typename cplx<R>::
     const int tid = threadIdx.x;
     const int o = blockIdx.y;
     const int i_base = blockIdx.x * (2 * NSEQ);
+    in0 += blockIdx.z * in_bstride;
+    if (in1) in1 += blockIdx.z * in_bstride;
+    out += blockIdx.z * out_bstride;
 
     for (int e = tid; e < NSEQ * P; e += NT) {
         const int s = e % NSEQ, k = e / NSEQ;
@@ -159,44 +166,45 @@ template <typename R> constexpr int nseq_for(int logp) {
 
 template <typename R, int LOGP, bool VEC>
 cudaError_t r2c_launch(const R* in, size_t in_ostride, size_t in_istride, int l_in, int I, int O, void* out, int i_pad,
-                       const void* tw, int log_t, cudaStream_t s) {
+                       const void* tw, int log_t, cudaStream_t s, Batch b) {
     using C = typename cplx<R>::type;
     constexpr int NSEQ = nseq_for<R>(LOGP);
     constexpr int NT = 512;
     const size_t smem = (size_t)NSEQ * seq_stride<C>(1 << LOGP) * sizeof(C);
-    auto k = row_r2c_kernel<R, LOGP, NSEQ, NT, VEC>;
-    cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    constexpr auto k = row_r2c_kernel<R, LOGP, NSEQ, NT, VEC>;
+    cudaError_t e = ensure_smem_limit<k>();
     if (e != cudaSuccess) return e;
-    dim3 grid((I + 2 * NSEQ - 1) / (2 * NSEQ), O);
-    k<<<grid, NT, smem, s>>>(in, in_ostride, in_istride, l_in, I, O, (C*)out, i_pad, (const C*)tw, log_t - LOGP);
+    dim3 grid((I + 2 * NSEQ - 1) / (2 * NSEQ), O, b.count);
+    k<<<grid, NT, smem, s>>>(in, in_ostride, in_istride, l_in, I, O, (C*)out, i_pad, (const C*)tw, log_t - LOGP, b.in,
+                             b.out);
     return cudaGetLastError();
 }
 
 template <typename R, int LOGP>
 cudaError_t r2c_impl(const R* in, size_t in_ostride, size_t in_istride, int l_in, int I, int O, void* out, int i_pad,
-                     const void* tw, int log_t, cudaStream_t s) {
+                     const void* tw, int log_t, cudaStream_t s, Batch b) {
     // float rows of at most P/2 values, whole 16-byte vectors, aligned
     if constexpr (sizeof(R) == 4) {
         const bool vec = l_in <= (1 << LOGP) / 2 && l_in % 2 == 0 && in_istride % 2 == 0 && in_ostride % 2 == 0 &&
-                         (reinterpret_cast<uintptr_t>(in) & 7) == 0 && i_pad % 2 == 0;
-        if (vec) return r2c_launch<R, LOGP, true>(in, in_ostride, in_istride, l_in, I, O, out, i_pad, tw, log_t, s);
+                         b.in % 2 == 0 && (reinterpret_cast<uintptr_t>(in) & 7) == 0 && i_pad % 2 == 0;
+        if (vec) return r2c_launch<R, LOGP, true>(in, in_ostride, in_istride, l_in, I, O, out, i_pad, tw, log_t, s, b);
     }
-    return r2c_launch<R, LOGP, false>(in, in_ostride, in_istride, l_in, I, O, out, i_pad, tw, log_t, s);
+    return r2c_launch<R, LOGP, false>(in, in_ostride, in_istride, l_in, I, O, out, i_pad, tw, log_t, s, b);
 }
 
 template <typename R, int LOGP>
 cudaError_t c2r_impl(const void* in0, const void* in1, int I, int O, int i_pad, R* out, size_t out_stride, int l_out,
-                     const void* tw, int log_t, cudaStream_t s) {
+                     const void* tw, int log_t, cudaStream_t s, Batch b) {
     using C = typename cplx<R>::type;
     constexpr int NSEQ = nseq_for<R>(LOGP);
     constexpr int NT = 512;
     const size_t smem = (size_t)NSEQ * seq_stride<C>(1 << LOGP) * sizeof(C);
-    auto k = row_c2r_kernel<R, LOGP, NSEQ, NT>;
-    cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    constexpr auto k = row_c2r_kernel<R, LOGP, NSEQ, NT>;
+    cudaError_t e = ensure_smem_limit<k>();
     if (e != cudaSuccess) return e;
-    dim3 grid((I + 2 * NSEQ - 1) / (2 * NSEQ), O);
+    dim3 grid((I + 2 * NSEQ - 1) / (2 * NSEQ), O, b.count);
     k<<<grid, NT, smem, s>>>((const C*)in0, (const C*)in1, I, O, i_pad, out, out_stride, l_out, (const C*)tw,
-                             log_t - LOGP);
+                             log_t - LOGP, b.in, b.out);
     return cudaGetLastError();
 }
 
@@ -206,10 +214,10 @@ cudaError_t c2r_impl(const void* in0, const void* in1, int I, int O, int i_pad, 
 
 template <typename R>
 cudaError_t launch_row_r2c(int log_p, const R* in, size_t in_ostride, size_t in_istride, int l_in, int I, int O,
-                           void* out, int i_pad, const void* tw, int log_t, cudaStream_t s) {
+                           void* out, int i_pad, const void* tw, int log_t, cudaStream_t s, Batch b) {
     switch (log_p) {
 #define CASE(L) \
-    case L: return r2c_impl<R, L>(in, in_ostride, in_istride, l_in, I, O, out, i_pad, tw, log_t, s);
+    case L: return r2c_impl<R, L>(in, in_ostride, in_istride, l_in, I, O, out, i_pad, tw, log_t, s, b);
         GRAV_LOGP_CASES(CASE)
 #undef CASE
         default: return cudaErrorInvalidValue;
@@ -218,10 +226,10 @@ cudaError_t launch_row_r2c(int log_p, const R* in, size_t in_ostride, size_t in_
 
 template <typename R>
 cudaError_t launch_row_c2r(int log_p, const void* in0, const void* in1, int I, int O, int i_pad, R* out,
-                           size_t out_stride, int l_out, const void* tw, int log_t, cudaStream_t s) {
+                           size_t out_stride, int l_out, const void* tw, int log_t, cudaStream_t s, Batch b) {
     switch (log_p) {
 #define CASE(L) \
-    case L: return c2r_impl<R, L>(in0, in1, I, O, i_pad, out, out_stride, l_out, tw, log_t, s);
+    case L: return c2r_impl<R, L>(in0, in1, I, O, i_pad, out, out_stride, l_out, tw, log_t, s, b);
         GRAV_LOGP_CASES(CASE)
 #undef CASE
         default: return cudaErrorInvalidValue;
@@ -229,12 +237,12 @@ cudaError_t launch_row_c2r(int log_p, const void* in0, const void* in1, int I, i
 }
 
 template cudaError_t launch_row_r2c<float>(int, const float*, size_t, size_t, int, int, int, void*, int, const void*,
-                                           int, cudaStream_t);
+                                           int, cudaStream_t, Batch);
 template cudaError_t launch_row_r2c<double>(int, const double*, size_t, size_t, int, int, int, void*, int,
-                                            const void*, int, cudaStream_t);
+                                            const void*, int, cudaStream_t, Batch);
 template cudaError_t launch_row_c2r<float>(int, const void*, const void*, int, int, int, float*, size_t, int,
-                                           const void*, int, cudaStream_t);
+                                           const void*, int, cudaStream_t, Batch);
 template cudaError_t launch_row_c2r<double>(int, const void*, const void*, int, int, int, double*, size_t, int,
-                                            const void*, int, cudaStream_t);
+                                            const void*, int, cudaStream_t, Batch);
 
 }  // namespace grav

@@ -4,6 +4,7 @@
 #include <stddef.h>
 #include <stdint.h>
 
+#include <atomic>
 #include <vector>
 
 #include "../../include/grav.h"
@@ -83,6 +84,33 @@ struct grav_plan {
 
 namespace grav {
 
+// Largest dynamic shared memory a CTA may use on sm_103a.
+constexpr int kMaxSmemOptin = 227 * 1024;
+
+// Raise a kernel's dynamic shared-memory limit to kMaxSmemOptin once per
+// device (a kernel instance needs it before its first launch with more than
+// 48 KB); later launches, including ones being captured into a CUDA graph,
+// make no attribute call.
+template <auto Kernel>
+inline cudaError_t ensure_smem_limit() {
+    static std::atomic<unsigned long long> done{0};
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    const unsigned long long bit = 1ull << (dev & 63);
+    if (done.load(std::memory_order_acquire) & bit) return cudaSuccess;
+    e = cudaFuncSetAttribute(Kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, kMaxSmemOptin);
+    if (e == cudaSuccess) done.fetch_or(bit, std::memory_order_acq_rel);
+    return e;
+}
+
+// Per-request strides of a batched call (elements of the buffer's own type);
+// unused when batch == 1.
+struct Batch {
+    int count = 1;
+    size_t in = 0, out = 0;
+};
+
 // Thread-local error message and CUDA check helpers (capi.cu).
 void set_error(const char* fmt, ...);
 int cuda_fail(cudaError_t e, const char* what);
@@ -101,31 +129,31 @@ cudaError_t launch_kernel_gen(const Geometry& g, unsigned comps, int n0, int n1,
 template <typename R>
 cudaError_t launch_row_r2c(int log_p, const R* in, size_t in_ostride, size_t in_istride,
                            int l_in, int I, int O, void* out, int i_pad, const void* tw,
-                           int log_t, cudaStream_t s);
+                           int log_t, cudaStream_t s, Batch b = Batch());
 // Half spectra (the sum of in0 and in1, layout as above) -> real rows:
 //   out row (o, i) at out + (o * I + i) * out_stride, first l_out values.
 template <typename R>
 cudaError_t launch_row_c2r(int log_p, const void* in0, const void* in1, int I, int O, int i_pad,
                            R* out, size_t out_stride, int l_out, const void* tw, int log_t,
-                           cudaStream_t s);
+                           cudaStream_t s, Batch b = Batch());
 
 // ---- column kernels (spectral.cuh, col_*.cu) ----
 // err: device int set to 1 when a pipeline wait ran out (the kernel then
 // leaves early and its output is invalid).
 template <typename R>
 cudaError_t launch_forward_columns(int log_n, const ColumnArgs& a, const void* X, const R* spec,
-                                   void* Y, const void* tw, int* err, cudaStream_t s);
+                                   void* Y, const void* tw, int* err, cudaStream_t s, Batch b);
 template <typename R>
 cudaError_t launch_adjoint_columns(int log_n, const ColumnArgs& a, const void* Xr, const R* spec,
-                                   void* Z, const void* tw, cudaStream_t s);
+                                   void* Z, const void* tw, int* err, cudaStream_t s, Batch b);
 template <> cudaError_t launch_forward_columns<float>(int, const ColumnArgs&, const void*, const float*, void*,
-                                                     const void*, int*, cudaStream_t);
+                                                     const void*, int*, cudaStream_t, Batch);
 template <> cudaError_t launch_forward_columns<double>(int, const ColumnArgs&, const void*, const double*, void*,
-                                                      const void*, int*, cudaStream_t);
+                                                      const void*, int*, cudaStream_t, Batch);
 template <> cudaError_t launch_adjoint_columns<float>(int, const ColumnArgs&, const void*, const float*, void*,
-                                                     const void*, cudaStream_t);
+                                                     const void*, int*, cudaStream_t, Batch);
 template <> cudaError_t launch_adjoint_columns<double>(int, const ColumnArgs&, const void*, const double*, void*,
-                                                      const void*, cudaStream_t);
+                                                      const void*, int*, cudaStream_t, Batch);
 // Column FFT of embedded kernel row transforms and extraction of the stored
 // real numbers.  Ehat[kx][o][b] (b < py, row stride py), o = c * nzc + n.
 template <typename RO>

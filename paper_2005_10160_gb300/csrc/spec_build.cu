@@ -63,8 +63,8 @@ cudaError_t extract_impl(const void* ehat, int kx_count, int nzc, int ncomp, int
                          unsigned imag_mask, double scale, RO* spec, const void* tw64, int log_t, cudaStream_t s) {
     constexpr int NT = 128;
     const size_t smem = (size_t)spad_len<double2>(1 << LOGN) * sizeof(double2);
-    auto k = spec_extract_kernel<RO, LOGN, NT>;
-    cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    constexpr auto k = spec_extract_kernel<RO, LOGN, NT>;
+    cudaError_t e = ensure_smem_limit<k>();
     if (e != cudaSuccess) return e;
     dim3 grid(kx_count, 2, ncomp * nzc);
     k<<<grid, NT, smem, s>>>((const double2*)ehat, kx_count, nzc, ncomp, n0, nz, jp, imag_mask, scale, spec,

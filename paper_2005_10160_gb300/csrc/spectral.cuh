@@ -97,7 +97,8 @@ template <typename R, int LOGN, int NC>
 __global__ void __launch_bounds__(ColShape<LOGN>::J, ColShape<LOGN>::J <= 256 ? 2 : 1)
     forward_column_kernel(ColumnArgs a, FwdSmem L, const typename cplx<R>::type* __restrict__ X,
                           const R* __restrict__ spec, typename cplx<R>::type* __restrict__ Y,
-                          const typename cplx<R>::type* __restrict__ tw, int* __restrict__ err) {
+                          const typename cplx<R>::type* __restrict__ tw, int* __restrict__ err, size_t x_bstride,
+                          size_t y_bstride) {
     using C = typename cplx<R>::type;
     constexpr int N = 1 << LOGN, J = ColShape<LOGN>::J, NT = J;
     constexpr int NSEQ = FwdCfg<R>::NSEQ;
@@ -115,6 +116,8 @@ __global__ void __launch_bounds__(ColShape<LOGN>::J, ColShape<LOGN>::J <= 256 ? 
     const int grp = tid / NTG, lt = tid - grp * NTG;
     const int r = blockIdx.x & 1, kx = blockIdx.x >> 1;
     const int nz = a.nz, ny = a.ny, depth = L.depth;
+    X += blockIdx.y * x_bstride;  // request of a batched call
+    Y += blockIdx.y * y_bstride;
     const C* Xk = X + (size_t)kx * nz * a.ny_pad;
     const size_t s_row = (size_t)a.ncomp * a.jp;
     const R* Sk = spec + (size_t)(r * a.kx_count + kx) * nz * s_row;
@@ -303,7 +306,8 @@ __global__ void __launch_bounds__(ColShape<LOGN>::J, ColShape<LOGN>::J <= 256 ? 
 template <typename R, int LOGN, int CPG>
 __global__ void __launch_bounds__(ColShape<LOGN>::NT, 1)
     adjoint_column_kernel(ColumnArgs a, const typename cplx<R>::type* __restrict__ Xr, const R* __restrict__ spec,
-                          typename cplx<R>::type* __restrict__ Z, const typename cplx<R>::type* __restrict__ tw) {
+                          typename cplx<R>::type* __restrict__ Z, const typename cplx<R>::type* __restrict__ tw,
+                          size_t x_bstride, size_t z_bstride) {
     using C = typename cplx<R>::type;
     using S = ColShape<LOGN>;
     constexpr int N = S::N, J = S::J, H = S::H, TG = S::TG, NT = S::NT, XPT = S::XPT;
@@ -315,6 +319,8 @@ __global__ void __launch_bounds__(ColShape<LOGN>::NT, 1)
     const int tid = threadIdx.x;
     const int g = tid / TG, lt = tid - g * TG;
     const int kx = blockIdx.x, r = blockIdx.y;
+    Xr += blockIdx.z * x_bstride;  // request of a batched call
+    Z += blockIdx.z * z_bstride;
     const R* sp = spec + (size_t)(r * a.kx_count + kx) * a.nz * a.ncomp * a.jp;
     const bool has_nyq = (r == 0 && lt == 0);
 

@@ -5,36 +5,35 @@
 
 namespace grav {
 
-constexpr int kMaxSmemPerCta = 227 * 1024;
-
 template <typename R, int LOGN, int NC>
 cudaError_t forward_impl(const ColumnArgs& a, const void* X, const R* spec, void* Y, const void* tw, int* err,
-                         cudaStream_t s) {
+                         cudaStream_t s, Batch b) {
     using C = typename cplx<R>::type;
-    const FwdSmem L = forward_smem<R>(LOGN, a.ny_pad, a.ncomp, a.jp, kMaxSmemPerCta);
+    const FwdSmem L = forward_smem<R>(LOGN, a.ny_pad, a.ncomp, a.jp, kMaxSmemOptin);
     if (L.depth == 0) return cudaErrorInvalidConfiguration;
-    auto k = forward_column_kernel<R, LOGN, NC>;
-    cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)L.total);
+    constexpr auto k = forward_column_kernel<R, LOGN, NC>;
+    cudaError_t e = ensure_smem_limit<k>();
     if (e != cudaSuccess) return e;
-    k<<<dim3(2 * a.kx_count), ColShape<LOGN>::J, L.total, s>>>(a, L, (const C*)X, spec, (C*)Y, (const C*)tw, err);
+    k<<<dim3(2 * a.kx_count, b.count), ColShape<LOGN>::J, L.total, s>>>(a, L, (const C*)X, spec, (C*)Y, (const C*)tw,
+                                                                         err, b.in, b.out);
     return cudaGetLastError();
 }
 
 #define GRAV_NC_SWITCH(R, L)                                                     \
     switch (nc_for(a.ncomp)) {                                                   \
-        case 1: return forward_impl<R, L, 1>(a, in, spec, out, tw, err, s);      \
-        case 2: return forward_impl<R, L, 2>(a, in, spec, out, tw, err, s);      \
-        case 3: return forward_impl<R, L, 3>(a, in, spec, out, tw, err, s);      \
-        case 4: return forward_impl<R, L, 4>(a, in, spec, out, tw, err, s);      \
-        case 5: return forward_impl<R, L, 5>(a, in, spec, out, tw, err, s);      \
-        case 6: return forward_impl<R, L, 6>(a, in, spec, out, tw, err, s);      \
-        default: return forward_impl<R, L, 7>(a, in, spec, out, tw, err, s);     \
+        case 1: return forward_impl<R, L, 1>(a, in, spec, out, tw, err, s, b);   \
+        case 2: return forward_impl<R, L, 2>(a, in, spec, out, tw, err, s, b);   \
+        case 3: return forward_impl<R, L, 3>(a, in, spec, out, tw, err, s, b);   \
+        case 4: return forward_impl<R, L, 4>(a, in, spec, out, tw, err, s, b);   \
+        case 5: return forward_impl<R, L, 5>(a, in, spec, out, tw, err, s, b);   \
+        case 6: return forward_impl<R, L, 6>(a, in, spec, out, tw, err, s, b);   \
+        default: return forward_impl<R, L, 7>(a, in, spec, out, tw, err, s, b);  \
     }
 
 #define GRAV_FORWARD_LAUNCHER(R)                                                                        \
     template <>                                                                                         \
     cudaError_t launch_forward_columns<R>(int log_n, const ColumnArgs& a, const void* in, const R* spec, \
-                                          void* out, const void* tw, int* err, cudaStream_t s) {        \
+                                          void* out, const void* tw, int* err, cudaStream_t s, Batch b) { \
         switch (log_n) {                                                                                \
             case 1: GRAV_NC_SWITCH(R, 1)                                                                \
             case 2: GRAV_NC_SWITCH(R, 2)                                                                \
@@ -51,13 +50,16 @@ cudaError_t forward_impl(const ColumnArgs& a, const void* X, const R* spec, void
     }
 
 template <typename R, int LOGN, int CPG>
-cudaError_t adjoint_impl(const ColumnArgs& a, const void* Xr, const R* spec, void* Z, const void* tw, cudaStream_t s) {
+cudaError_t adjoint_impl(const ColumnArgs& a, const void* Xr, const R* spec, void* Z, const void* tw, int* err,
+                         cudaStream_t s, Batch b) {
     using C = typename cplx<R>::type;
-    auto k = adjoint_column_kernel<R, LOGN, CPG>;
+    (void)err;
+    constexpr auto k = adjoint_column_kernel<R, LOGN, CPG>;
     const size_t smem = column_smem_bytes<R>(LOGN);
-    cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaError_t e = ensure_smem_limit<k>();
     if (e != cudaSuccess) return e;
-    k<<<dim3(a.kx_count, 2), ColShape<LOGN>::NT, smem, s>>>(a, (const C*)Xr, spec, (C*)Z, (const C*)tw);
+    k<<<dim3(a.kx_count, 2, b.count), ColShape<LOGN>::NT, smem, s>>>(a, (const C*)Xr, spec, (C*)Z, (const C*)tw, b.in,
+                                                                       b.out);
     return cudaGetLastError();
 }
 
@@ -72,18 +74,18 @@ cudaError_t adjoint_impl(const ColumnArgs& a, const void* Xr, const R* spec, voi
 #define GRAV_COLUMN_LAUNCHER(NAME, IMPL, R)                                                              \
     template <>                                                                                          \
     cudaError_t NAME<R>(int log_n, const ColumnArgs& a, const void* in, const R* spec, void* out,       \
-                        const void* tw, cudaStream_t s) {                                                \
+                        const void* tw, int* err, cudaStream_t s, Batch b) {                             \
         switch (log_n) {                                                                                 \
-            case 1: GRAV_CPG_SWITCH(IMPL, R, 1, a, in, spec, out, tw, s)                                 \
-            case 2: GRAV_CPG_SWITCH(IMPL, R, 2, a, in, spec, out, tw, s)                                 \
-            case 3: GRAV_CPG_SWITCH(IMPL, R, 3, a, in, spec, out, tw, s)                                 \
-            case 4: GRAV_CPG_SWITCH(IMPL, R, 4, a, in, spec, out, tw, s)                                 \
-            case 5: GRAV_CPG_SWITCH(IMPL, R, 5, a, in, spec, out, tw, s)                                 \
-            case 6: GRAV_CPG_SWITCH(IMPL, R, 6, a, in, spec, out, tw, s)                                 \
-            case 7: GRAV_CPG_SWITCH(IMPL, R, 7, a, in, spec, out, tw, s)                                 \
-            case 8: GRAV_CPG_SWITCH(IMPL, R, 8, a, in, spec, out, tw, s)                                 \
-            case 9: GRAV_CPG_SWITCH(IMPL, R, 9, a, in, spec, out, tw, s)                                 \
-            case 10: GRAV_CPG_SWITCH(IMPL, R, 10, a, in, spec, out, tw, s)                               \
+            case 1: GRAV_CPG_SWITCH(IMPL, R, 1, a, in, spec, out, tw, err, s, b)                                 \
+            case 2: GRAV_CPG_SWITCH(IMPL, R, 2, a, in, spec, out, tw, err, s, b)                                 \
+            case 3: GRAV_CPG_SWITCH(IMPL, R, 3, a, in, spec, out, tw, err, s, b)                                 \
+            case 4: GRAV_CPG_SWITCH(IMPL, R, 4, a, in, spec, out, tw, err, s, b)                                 \
+            case 5: GRAV_CPG_SWITCH(IMPL, R, 5, a, in, spec, out, tw, err, s, b)                                 \
+            case 6: GRAV_CPG_SWITCH(IMPL, R, 6, a, in, spec, out, tw, err, s, b)                                 \
+            case 7: GRAV_CPG_SWITCH(IMPL, R, 7, a, in, spec, out, tw, err, s, b)                                 \
+            case 8: GRAV_CPG_SWITCH(IMPL, R, 8, a, in, spec, out, tw, err, s, b)                                 \
+            case 9: GRAV_CPG_SWITCH(IMPL, R, 9, a, in, spec, out, tw, err, s, b)                                 \
+            case 10: GRAV_CPG_SWITCH(IMPL, R, 10, a, in, spec, out, tw, err, s, b)                               \
             default: return cudaErrorInvalidValue;                                                       \
         }                                                                                                \
     }

@@ -59,15 +59,15 @@ int forward_static(grav_plan* p, const void* rho, void* out, unsigned char* scra
     void* X = scratch;
     void* Y = scratch + x_bytes;
     cudaError_t e = launch_row_r2c<R>(p->log_px, (const R*)rho, (size_t)p->ny * p->nx, (size_t)p->nx, p->nx, p->ny,
-                                      p->nz, X, p->ny_pad, p->tw, p->log_t, s);
+                                      p->nz, X, p->ny_pad, p->tw, p->log_t, s, Batch());
     if (e != cudaSuccess) return cuda_fail(e, "static-scratch forward row transform");
     ColumnArgs a{p->ny, p->ny_pad, p->nz, p->ncomp, p->kx_count, p->jp, p->imag_mask, p->oddv_mask,
                  p->log_t - (p->log_py - 1), p->log_t - p->log_py};
-    e = launch_forward_columns<R>(p->log_py - 1, a, X, (const R*)p->spec, Y, p->tw, p->err_flag, s);
+    e = launch_forward_columns<R>(p->log_py - 1, a, X, (const R*)p->spec, Y, p->tw, p->err_flag, s, Batch());
     if (e != cudaSuccess) return cuda_fail(e, "static-scratch forward column stage");
     const size_t half = (size_t)p->kx_count * p->ncomp * p->ny_pad * 2 * sizeof(R);
     e = launch_row_c2r<R>(p->log_px, Y, (const unsigned char*)Y + half, p->ny, p->ncomp, p->ny_pad, (R*)out,
-                          (size_t)p->nx, p->nx, p->tw, p->log_t, s);
+                          (size_t)p->nx, p->nx, p->tw, p->log_t, s, Batch());
     if (e != cudaSuccess) return cuda_fail(e, "static-scratch forward inverse row transform");
     return GRAV_OK;
 }
