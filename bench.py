@@ -38,6 +38,7 @@ sys.path.insert(0, ROOT)
 WORKLOADS = {
     # name: (nx, ny, nz, dx, dy, dz, h)
     "grf1024": (1024, 1024, 100, 50.0, 50.0, 25.0, 10.0),
+    "grf1024z16": (1024, 1024, 16, 50.0, 50.0, 25.0, 10.0),  # same kernels, fewer layers (profiling)
     "boxes512": (512, 512, 64, 20.0, 20.0, 20.0, 10.0),
     "boxes256": (256, 256, 32, 25.0, 25.0, 20.0, 5.0),
 }
@@ -337,7 +338,7 @@ def run_ours(args):
     nx, ny, nz = mesh[:3]
     pairs = pairs_per_forward(mesh)
 
-    if args.workload == "grf1024":
+    if args.workload.startswith("grf1024"):
         _, rho = workloads.grf1024(nx, ny, nz, device=dev)
     else:
         m = workloads.Mesh(*mesh)

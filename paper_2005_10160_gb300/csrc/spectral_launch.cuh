@@ -2,6 +2,7 @@
 // (transform length, components per thread group).
 #pragma once
 #include "spectral.cuh"
+#include "spectral_ws.cuh"
 
 namespace grav {
 
@@ -9,6 +10,18 @@ template <typename R, int LOGN, int NC>
 cudaError_t forward_impl(const ColumnArgs& a, const void* X, const R* spec, void* Y, const void* tw, int* err,
                          cudaStream_t s, Batch b) {
     using C = typename cplx<R>::type;
+    if constexpr (sizeof(R) == 4 && (LOGN == 9 || LOGN == 10)) {
+        // large FP32 transforms: the warp-specialised kernel
+        const WsSmem W = ws_smem<LOGN>(a.ny_pad, a.ncomp, a.jp, NC, kMaxSmemOptin);
+        if (W.ds != 0) {
+            constexpr auto kw = forward_column_ws_kernel<LOGN, NC>;
+            cudaError_t e = ensure_smem_limit<kw>();
+            if (e != cudaSuccess) return e;
+            kw<<<dim3(2 * a.kx_count, b.count), WsShape<LOGN>::NT, W.total, s>>>(
+                a, W, (const float2*)X, (const float*)spec, (float2*)Y, (const float2*)tw, err, b.in, b.out);
+            return cudaGetLastError();
+        }
+    }
     const FwdSmem L = forward_smem<R>(LOGN, a.ny_pad, a.ncomp, a.jp, kMaxSmemOptin);
     if (L.depth == 0) return cudaErrorInvalidConfiguration;
     constexpr auto k = forward_column_kernel<R, LOGN, NC>;
