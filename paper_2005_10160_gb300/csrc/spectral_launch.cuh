@@ -2,6 +2,7 @@
 // (transform length, components per thread group).
 #pragma once
 #include "spectral.cuh"
+#include "spectral_wf.cuh"
 #include "spectral_ws.cuh"
 
 namespace grav {
@@ -10,6 +11,18 @@ template <typename R, int LOGN, int NC>
 cudaError_t forward_impl(const ColumnArgs& a, const void* X, const R* spec, void* Y, const void* tw, int* err,
                          cudaStream_t s, Batch b) {
     using C = typename cplx<R>::type;
+    if constexpr (sizeof(R) == 4 && LOGN == 10 && NC <= WfShape::FWARPS) {
+        // 1024-point FP32 columns: one warp per layer transform
+        const WfSmem W = wf_smem(a.ny_pad, a.ncomp, a.jp, NC, kMaxSmemOptin);
+        if (W.df != 0) {
+            constexpr auto kw = forward_column_wf_kernel<NC>;
+            cudaError_t e = ensure_smem_limit<kw>();
+            if (e != cudaSuccess) return e;
+            kw<<<dim3(2 * a.kx_count, b.count), WfShape::NT, W.total, s>>>(
+                a, W, (const float2*)X, (const float*)spec, (float2*)Y, (const float2*)tw, err, b.in, b.out);
+            return cudaGetLastError();
+        }
+    }
     if constexpr (sizeof(R) == 4 && (LOGN == 9 || LOGN == 10)) {
         // large FP32 transforms: the warp-specialised kernel
         const WsSmem W = ws_smem<LOGN>(a.ny_pad, a.ncomp, a.jp, NC, kMaxSmemOptin);

@@ -1,0 +1,378 @@
+// Forward column stage for 1024-point FP32 column transforms (Py = 2048)
+// with one warp per layer transform.
+//
+// 24 warps at 80 registers a thread (the whole register file: 768 x 80, six
+// warps per SM sub-partition).  Warps 0-15 accumulate: thread q owns mirror
+// pair q for every component (the layer sum of Eq. 20 in the Fourier
+// domain).  Warps 16-23 transform: each layer's 1024-point FFT is done by a
+// single warp in registers, 32 values a lane, as 1024 = 32 x 32 (the
+// four-step form):
+//   x[32 n1 + n2] -> 32-point DFTs over n1 (lane n2) -> twiddle W_1024^(n2 k1)
+//   -> transpose through shared memory -> 32-point DFTs over n2 (lane k1).
+// A warp transform needs no block or group barrier, so eight layers are in
+// flight at once and the transform costs about a third of the instructions
+// of a shared-memory radix-8 transform by a thread group.
+//
+// Data movement: FFT warp f handles layers f, f + 8, ...; X slot f is its
+// own, so after reading layer n it refills the slot with layer n + 8 itself
+// (bulk copy) and prefetches a later layer's spectra into L2.  The
+// accumulate threads read their spectra values from global memory one layer
+// ahead, in registers.  The spectra value of the Nyquist row (one per
+// component, used by one thread of the even-ky CTA) rides in the spare tail
+// of the layer's F slot.  Every wait is bounded.
+#pragma once
+#include "async_copy.cuh"
+#include "fft_block.cuh"
+#include "grav_internal.h"
+#include "spectral.cuh"
+#include "spectral_ws.cuh"
+
+namespace grav {
+
+struct WfShape {
+    static constexpr int N = 1024;
+    static constexpr int J = 512;          // accumulate threads (16 warps)
+    static constexpr int FWARPS = 8;       // FFT warps (2 warpgroups)
+    static constexpr int NT = J + 32 * FWARPS;
+    static constexpr int FSLOT = 32 * 33;  // complex values per F slot (transpose area)
+    static constexpr int REGS = 80;        // registers a thread: NT x REGS = 61440
+    static constexpr int DX = FWARPS;      // one X slot per FFT warp
+    static constexpr int PF = 16;          // spectra prefetch distance (layers)
+};
+
+struct WfSmem {
+    int df;
+    uint32_t x_bytes, s_bytes, f_bytes;
+    uint32_t f_off, tw_off, t2_off, cmp_off, bar_off, flag_off, total;
+};
+
+// cos(2 pi j / 32) for any integer j (exact symmetries of the first octant).
+__device__ __forceinline__ float cos32(int j) {
+    const float b[9] = {1.0f,
+                        0.980785280403230449126f,
+                        0.923879532511286756128f,
+                        0.831469612302545237079f,
+                        0.707106781186547524401f,
+                        0.555570233019602224743f,
+                        0.382683432365089771729f,
+                        0.195090322016128267848f,
+                        0.0f};
+    j &= 31;
+    if (j <= 8) return b[j];
+    if (j <= 16) return -b[16 - j];
+    if (j <= 24) return -b[j - 16];
+    return b[32 - j];
+}
+
+// a * W_32^j with W_32 = exp(-+ 2 pi i / 32) (inverse: +); j is a constant
+// after unrolling, so the branches and the cosines fold away.
+template <bool INV> __device__ __forceinline__ float2 tw32(float2 a, int j) {
+    j &= 31;
+    if (j == 0) return a;
+    if (j == 16) return make_float2(-a.x, -a.y);
+    if (j == 8) return INV ? make_float2(-a.y, a.x) : make_float2(a.y, -a.x);
+    if (j == 24) return INV ? make_float2(a.y, -a.x) : make_float2(-a.y, a.x);
+    const float c = cos32(j), s = INV ? cos32(j - 8) : -cos32(j - 8);  // sin(2 pi j/32) = cos(2 pi (j-8)/32)
+    return make_float2(a.x * c - a.y * s, a.x * s + a.y * c);
+}
+
+__host__ __device__ constexpr int bitrev5(int j) {
+    return ((j & 1) << 4) | ((j & 2) << 2) | (j & 4) | ((j & 8) >> 2) | ((j & 16) >> 4);
+}
+
+// 32-point DFT in registers, radix-2 decimation in frequency: natural order
+// in, u[j] = X[bitrev5(j)] out.
+template <bool INV> __device__ __forceinline__ void dft32(float2 (&u)[32]) {
+#pragma unroll
+    for (int h = 16; h >= 1; h >>= 1) {
+#pragma unroll
+        for (int b = 0; b < 32; b += 2 * h) {
+#pragma unroll
+            for (int i = 0; i < h; ++i) {
+                const float2 a = u[b + i], c = u[b + i + h];
+                u[b + i] = make_float2(a.x + c.x, a.y + c.y);
+                u[b + i + h] = tw32<INV>(make_float2(a.x - c.x, a.y - c.y), i * (16 / h));
+            }
+        }
+    }
+}
+
+// 1024-point FFT by one warp.  In: u[n1] = x[32 n1 + lane].  Out: u[j] =
+// X[lane + 32 bitrev5(j)].  tr: the warp's 32 x 33 transpose area; t2[k1 32 +
+// lane] = W_1024^(lane k1).  tr may be overwritten by the caller afterwards.
+template <bool INV>
+__device__ __forceinline__ void warp_fft1024(float2 (&u)[32], float2* tr, const float2* t2, int lane) {
+    dft32<INV>(u);
+#pragma unroll
+    for (int j = 0; j < 32; ++j) {
+        const int k1 = bitrev5(j);
+        float2 w = t2[k1 * 32 + lane];
+        if (INV) w.y = -w.y;
+        tr[k1 * 33 + lane] = cmul(u[j], w);
+    }
+    __syncwarp();
+#pragma unroll
+    for (int n2 = 0; n2 < 32; ++n2) u[n2] = tr[lane * 33 + n2];
+    __syncwarp();
+    dft32<INV>(u);
+}
+
+// CTA-wide barrier (id 1) that the two roles reach from their own code
+// (no .aligned: the arrivals come from different instructions), with an OR
+// of a predicate.
+__device__ __forceinline__ bool cta_sync_or(bool v) {
+    uint32_t out;
+    asm volatile(
+        "{\n\t.reg .pred p, q;\n\t"
+        "setp.ne.u32 p, %1, 0;\n\t"
+        "barrier.red.or.pred q, 1, p;\n\t"
+        "selp.u32 %0, 1, 0, q;\n\t}"
+        : "=r"(out)
+        : "r"((uint32_t)v)
+        : "memory");
+    return out != 0;
+}
+__device__ __forceinline__ void cta_sync() { asm volatile("barrier.sync 1;" ::: "memory"); }
+
+template <int NC>
+__global__ void __maxnreg__(WfShape::REGS)
+    forward_column_wf_kernel(ColumnArgs a, WfSmem L, const float2* __restrict__ X, const float* __restrict__ spec,
+                             float2* __restrict__ Y, const float2* __restrict__ tw, int* __restrict__ err,
+                             size_t x_bstride, size_t y_bstride) {
+    using C = float2;
+    constexpr int N = WfShape::N, J = WfShape::J, FW = WfShape::FWARPS, NT = WfShape::NT;
+    constexpr int FS = WfShape::FSLOT, DX = WfShape::DX, PF = WfShape::PF;
+    static_assert(NC <= FW, "one inverse transform per FFT warp");
+    static_assert(NC <= FS - N, "Nyquist spectra values fit in the F slot tail");
+    extern __shared__ __align__(128) unsigned char smem[];
+    unsigned char* xring = smem;
+    C* fring = reinterpret_cast<C*>(smem + L.f_off);
+    C* tws = reinterpret_cast<C*>(smem + L.tw_off);  // fold twiddles W_Py^m, m < N
+    C* t2 = reinterpret_cast<C*>(smem + L.t2_off);   // W_1024^(n2 k1) at [k1][n2]
+    float* cmp = reinterpret_cast<float*>(smem + L.cmp_off);  // Kahan corrections [c][j][q]
+    uint64_t* bars = reinterpret_cast<uint64_t*>(smem + L.bar_off);
+    uint64_t* xfull = bars;
+    uint64_t* ffull = xfull + DX;
+    uint64_t* fempty = ffull + L.df;
+    volatile int* abort = reinterpret_cast<volatile int*>(smem + L.flag_off);
+
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int r = blockIdx.x & 1, kx = blockIdx.x >> 1;
+    const int nz = a.nz, ny = a.ny;
+    X += blockIdx.y * x_bstride;  // request of a batched call
+    Y += blockIdx.y * y_bstride;
+    const C* Xk = X + (size_t)kx * nz * a.ny_pad;
+    const size_t s_row = (size_t)a.ncomp * a.jp;
+    const float* Sk = spec + (size_t)(r * a.kx_count + kx) * nz * s_row;
+
+    if (tid == 0) {
+        for (int s = 0; s < DX; ++s) mbar_init(&xfull[s], 1);
+        for (int s = 0; s < L.df; ++s) {
+            mbar_init(&ffull[s], 32);
+            mbar_init(&fempty[s], J);
+        }
+        *abort = 0;
+        fence_mbar_init();
+    }
+    for (int e = tid; e < N; e += NT) {
+        tws[e] = tw[e << a.tw_shift_p];
+        const int k1 = e >> 5, n2 = e & 31;
+        t2[e] = tw[((k1 * n2) & (N - 1)) << a.tw_shift_n];
+    }
+    for (int e = tid; e < 4 * NC * J; e += NT) cmp[e] = 0.f;
+    __syncthreads();
+    if (tid == 0) {
+        // first layer of every X slot, and the first PF layers' spectra into L2
+        for (int n = 0; n < DX && n < nz; ++n) {
+            mbar_arrive_expect_tx(&xfull[n], L.x_bytes);
+            bulk_g2s(xring + (size_t)n * L.x_bytes, Xk + (size_t)n * a.ny_pad, L.x_bytes, &xfull[n]);
+        }
+        for (int n = 0; n < PF && n < nz; ++n) bulk_prefetch_l2(Sk + (size_t)n * s_row, L.s_bytes);
+    }
+
+    bool failed = false;
+    const bool is_mac = tid < J;
+    const bool nyq = is_mac && r == 0 && tid == 0;
+
+    if (!is_mac) {
+        // ---------------- FFT warp f: layers f, f + FW, ... ----------------
+        const int f = warp - (J >> 5);
+        unsigned char* xslot = xring + (size_t)f * L.x_bytes;
+        const C* xs = reinterpret_cast<const C*>(xslot);
+        int pending = f < nz ? f : -1;  // layer of the copy in flight into X slot f
+        for (int n = f; n < nz; n += FW) {
+            const int sf = n % L.df;
+            int ok = 1;
+            if (lane == 0) {
+                ok = ws_wait(&xfull[f], (uint32_t)((n / DX) & 1), abort);
+                if (ok) pending = -1;
+                if (ok && n >= L.df) ok = ws_wait(&fempty[sf], (uint32_t)((n / L.df - 1) & 1), abort);
+            }
+            ok = __shfl_sync(0xffffffffu, ok, 0);
+            if (!ok) {
+                failed = true;
+                break;
+            }
+            float snyq = 0.f;  // Nyquist-row spectra value of component `lane`
+            if (r == 0 && lane < NC) snyq = __ldg(Sk + (size_t)n * s_row + lane * a.jp + J);
+            float2 u[32];
+#pragma unroll
+            for (int n1 = 0; n1 < 32; ++n1) {
+                const int m = 32 * n1 + lane;
+                C v = make_float2(0.f, 0.f);
+                if (m < ny) {
+                    v = xs[m];
+                    if (r) v = cmul(v, tws[m]);  // fold for ky parity r
+                }
+                u[n1] = v;
+            }
+            __syncwarp();  // every lane's reads of X slot f are done
+            if (lane == 0) {
+                if (n + FW < nz) {
+                    fence_proxy_async_smem();
+                    mbar_arrive_expect_tx(&xfull[f], L.x_bytes);
+                    bulk_g2s(xslot, Xk + (size_t)(n + FW) * a.ny_pad, L.x_bytes, &xfull[f]);
+                    pending = n + FW;
+                }
+                if (n + PF < nz) bulk_prefetch_l2(Sk + (size_t)(n + PF) * s_row, L.s_bytes);
+            }
+            C* fb = fring + sf * FS;
+            warp_fft1024<false>(u, fb, t2, lane);
+#pragma unroll
+            for (int j = 0; j < 32; ++j) fb[lane + 32 * bitrev5(j)] = u[j];
+            if (lane < NC) fb[N + lane] = make_float2(snyq, 0.f);
+            mbar_arrive(&ffull[sf]);  // this lane's writes of the F slot are done
+        }
+        if (lane == 0 && pending >= 0) {
+            // a copy that will not be consumed (failure path): let it land
+            // (bounded) before the CTA's shared memory is released
+            mbar_wait_bounded(&xfull[f], (uint32_t)((pending / DX) & 1), kWaitLimitNs);
+        }
+        if (cta_sync_or(failed || *abort)) return;
+        cta_sync();  // the accumulate threads have written the sums
+        // inverse column transform of component f (F slot f)
+        const int c = f;
+        if (c < NC) {
+            C* fb = fring + c * FS;
+            float2 u[32];
+#pragma unroll
+            for (int n1 = 0; n1 < 32; ++n1) u[n1] = fb[32 * n1 + lane];
+            __syncwarp();
+            warp_fft1024<true>(u, fb, t2, lane);
+            C* dst = Y + ((size_t)(r * a.kx_count + kx) * a.ncomp + c) * a.ny_pad;
+#pragma unroll
+            for (int j = 0; j < 32; ++j) {
+                const int y = lane + 32 * bitrev5(j);
+                if (y < ny) {
+                    C v = u[j];
+                    if (r) v = cmul(v, cconj(tws[y]));
+                    dst[y] = v;
+                }
+            }
+        }
+    } else {
+        // ---------------- accumulate: thread q owns mirror pair q ----------------
+        const int q = tid;
+        int k1 = 0, k2 = 0;
+        pair_pos<N>(q, r, k1, k2);
+        float acc[NC][4];
+#pragma unroll
+        for (int c = 0; c < NC; ++c)
+#pragma unroll
+            for (int j = 0; j < 4; ++j) acc[c][j] = 0.f;
+        float part[NC][4];
+#pragma unroll
+        for (int c = 0; c < NC; ++c)
+#pragma unroll
+            for (int j = 0; j < 4; ++j) part[c][j] = 0.f;
+        // this thread's spectra values Sk[n][c][q], loaded one layer ahead
+        const float* Sq = Sk + q;
+        float sv[NC];
+#pragma unroll
+        for (int c = 0; c < NC; ++c) sv[c] = nz > 0 ? __ldg(Sq + c * a.jp) : 0.f;
+        for (int n = 0; n < nz; ++n) {
+            const int sf = n % L.df;
+            if (!ws_wait(&ffull[sf], (uint32_t)((n / L.df) & 1), abort)) {
+                failed = true;
+                break;
+            }
+            const C* fb = fring + sf * FS;
+            const C v1 = fb[k1], v2 = fb[k2];
+#pragma unroll
+            for (int c = 0; c < NC; ++c) {
+                const float s2 = nyq ? fb[N + c].x : sv[c];
+                part[c][0] += sv[c] * v1.x;
+                part[c][1] += sv[c] * v1.y;
+                part[c][2] += s2 * v2.x;
+                part[c][3] += s2 * v2.y;
+            }
+            mbar_arrive(&fempty[sf]);
+            if (n + 1 < nz) {
+                const float* row = Sq + (size_t)(n + 1) * s_row;
+#pragma unroll
+                for (int c = 0; c < NC; ++c) sv[c] = __ldg(row + c * a.jp);
+            }
+            if ((n % kBlockLayers) == kBlockLayers - 1 || n == nz - 1) {
+#pragma unroll
+                for (int c = 0; c < NC; ++c)
+#pragma unroll
+                    for (int j = 0; j < 4; ++j) {
+                        float* cj = cmp + (c * 4 + j) * J + q;
+                        float cc = *cj;
+                        kahan_add(acc[c][j], cc, part[c][j]);
+                        *cj = cc;
+                        part[c][j] = 0.f;
+                    }
+            }
+        }
+        if (cta_sync_or(failed || *abort)) {
+            if (tid == 0) atomicExch(err, 1);
+            return;
+        }
+        // the compensated sums (times i for imaginary spectra, with the
+        // mirror sign for odd components) into F slot c, natural order
+#pragma unroll
+        for (int c = 0; c < NC; ++c) {
+            float e[4];
+#pragma unroll
+            for (int j = 0; j < 4; ++j) e[j] = acc[c][j] - cmp[(c * 4 + j) * J + q];
+            const bool imag = (a.imag_mask >> c) & 1u;
+            const bool flip = !nyq && ((a.oddv_mask >> c) & 1u);
+            C b1 = make_float2(e[0], e[1]), b2 = make_float2(e[2], e[3]);
+            if (flip) b2 = make_float2(-b2.x, -b2.y);
+            if (imag) {
+                b1 = make_float2(-b1.y, b1.x);
+                b2 = make_float2(-b2.y, b2.x);
+            }
+            C* fb = fring + c * FS;
+            fb[k1] = b1;
+            fb[k2] = b2;
+        }
+        cta_sync();
+    }
+}
+
+// Shared-memory layout; df == 0 when it does not fit.  The F ring holds
+// one slot per FFT warp plus the accumulate threads' lag.
+inline WfSmem wf_smem(int ny_pad, int ncomp, int jp, int nc_inst, int max_bytes) {
+    WfSmem L{};
+    L.x_bytes = (uint32_t)(ny_pad * sizeof(float2));
+    L.s_bytes = (uint32_t)(ncomp * jp * sizeof(float));
+    L.f_bytes = (uint32_t)(WfShape::FSLOT * sizeof(float2));
+    if (ny_pad > WfShape::N || nc_inst > WfShape::FWARPS || (L.x_bytes & 15u) || (L.s_bytes & 15u)) return WfSmem{};
+    for (int df = 12; df >= WfShape::FWARPS + 1; --df) {
+        WfSmem l = L;
+        l.df = df;
+        l.f_off = (uint32_t)(WfShape::DX * L.x_bytes + 127) & ~127u;
+        l.tw_off = l.f_off + df * L.f_bytes;
+        l.t2_off = l.tw_off + WfShape::N * sizeof(float2);
+        l.cmp_off = l.t2_off + WfShape::N * sizeof(float2);
+        l.bar_off = l.cmp_off + 4 * nc_inst * WfShape::J * sizeof(float);
+        l.flag_off = l.bar_off + (WfShape::DX + 2 * df) * 8;
+        l.total = l.flag_off + 16;
+        if ((int)l.total <= max_bytes) return l;
+    }
+    return WfSmem{};
+}
+
+}  // namespace grav

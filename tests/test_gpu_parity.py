@@ -183,6 +183,34 @@ def test_dot_product_adjoint(gravlib):
         assert abs(lhs - rhs) <= tol * max(abs(lhs), abs(rhs)), (fp64, lhs, rhs)
 
 
+# Meshes with 513 <= ny <= 1024: Py = 2048, so the FP32 forward runs the
+# 1024-point column kernel with one warp per layer transform (ragged ny_pad,
+# fewer layers than FFT warps, and enough layers to wrap every ring).
+WIDE_MESHES = [
+    (3, 1024, 20, 10.0, 10.0, 10.0, 2.0),
+    (5, 513, 9, 20.0, 15.0, 10.0, 3.0),
+    (2, 700, 1, 10.0, 10.0, 10.0, 1.0),
+]
+
+
+@pytest.mark.parametrize("mesh", WIDE_MESHES)
+@pytest.mark.parametrize("comps", [ALL7, 0x3F, capi.GRAV_GZ, capi.GRAV_GXY | capi.GRAV_GYZ])
+def test_forward_fp32_wide_columns(gravlib, orc, mesh, comps):
+    """FP32 forward on 2048-point columns: against the oracle at sampled
+    stations, and against the FP64 spectral path at every station."""
+    nx, ny, nz = mesh[:3]
+    rng = np.random.default_rng(nx * 1000 + ny + nz)
+    rho = rng.uniform(-300, 300, (nz, ny, nx))
+    got32 = run_forward(mesh, comps, rho, fp64=False).reshape(len(capi.comp_list(comps)), -1)
+    got64 = run_forward(mesh, comps, rho, fp64=True).reshape(len(capi.comp_list(comps)), -1)
+    st = np.unique(np.concatenate([[0, nx * ny - 1, nx * (ny // 2)],
+                                   rng.integers(0, nx * ny, 29)])).astype(np.int32)
+    ref = orc.forward(mesh, comps, rho, stations=st)
+    assert np.all(rel_errors(got32[:, st], ref, comps) <= TOL32)
+    assert np.all(rel_errors(got64[:, st], ref, comps) <= TOL64)
+    assert np.all(rel_errors(got32, got64, comps) <= TOL32)
+
+
 def test_repeatable_and_stream_ordered(gravlib):
     """Two calls give bit-identical results, on a non-default stream too."""
     mesh, rho = W.small16()

@@ -123,10 +123,10 @@ def test_request_beyond_the_budget_fails_cleanly(gravlib):
         srv.close()
 
 
-def test_batch_runner_matches_single_calls(gravlib):
+@pytest.mark.parametrize("mesh", [MESHES[2], W.Mesh(6, 600, 10, 20.0, 20.0, 10.0, 5.0)])
+def test_batch_runner_matches_single_calls(gravlib, mesh):
     """grav_forward_batch / grav_adjoint_batch with a caller workspace equal
-    per-request plain calls."""
-    mesh = MESHES[2]
+    per-request plain calls (the second mesh runs 2048-point columns)."""
     rng = np.random.default_rng(8)
     with Plan(mesh, capi.GRAV_ALL6) as plan:
         run = BatchRunner(plan)
