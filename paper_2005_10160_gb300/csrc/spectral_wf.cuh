@@ -37,7 +37,9 @@ struct WfShape {
     static constexpr int FSLOT = 32 * 33;  // complex values per F slot (transpose area)
     static constexpr int REGS = 80;        // registers a thread: NT x REGS = 61440
     static constexpr int DX = FWARPS;      // one X slot per FFT warp
-    static constexpr int PF = 16;          // spectra prefetch distance (layers)
+    static constexpr int PF = 8;           // spectra prefetch distance (layers)
+    static constexpr int JP = 516;         // spectra row pitch: J + 1 rounded up to 4
+    static constexpr int BLOCK = 16;       // layers per compensated block
 };
 
 struct WfSmem {
@@ -141,7 +143,8 @@ __global__ void __maxnreg__(WfShape::REGS)
                              size_t x_bstride, size_t y_bstride) {
     using C = float2;
     constexpr int N = WfShape::N, J = WfShape::J, FW = WfShape::FWARPS, NT = WfShape::NT;
-    constexpr int FS = WfShape::FSLOT, DX = WfShape::DX, PF = WfShape::PF;
+    constexpr int FS = WfShape::FSLOT, DX = WfShape::DX, PF = WfShape::PF, JP = WfShape::JP;
+    constexpr int S_ROW = NC * JP;  // floats per layer of spectra
     static_assert(NC <= FW, "one inverse transform per FFT warp");
     static_assert(NC <= FS - N, "Nyquist spectra values fit in the F slot tail");
     extern __shared__ __align__(128) unsigned char smem[];
@@ -162,8 +165,7 @@ __global__ void __maxnreg__(WfShape::REGS)
     X += blockIdx.y * x_bstride;  // request of a batched call
     Y += blockIdx.y * y_bstride;
     const C* Xk = X + (size_t)kx * nz * a.ny_pad;
-    const size_t s_row = (size_t)a.ncomp * a.jp;
-    const float* Sk = spec + (size_t)(r * a.kx_count + kx) * nz * s_row;
+    const float* Sk = spec + (size_t)(r * a.kx_count + kx) * nz * S_ROW;
 
     if (tid == 0) {
         for (int s = 0; s < DX; ++s) mbar_init(&xfull[s], 1);
@@ -187,7 +189,7 @@ __global__ void __maxnreg__(WfShape::REGS)
             mbar_arrive_expect_tx(&xfull[n], L.x_bytes);
             bulk_g2s(xring + (size_t)n * L.x_bytes, Xk + (size_t)n * a.ny_pad, L.x_bytes, &xfull[n]);
         }
-        for (int n = 0; n < PF && n < nz; ++n) bulk_prefetch_l2(Sk + (size_t)n * s_row, L.s_bytes);
+        for (int n = 0; n < PF && n < nz; ++n) bulk_prefetch_l2(Sk + (size_t)n * S_ROW, L.s_bytes);
     }
 
     bool failed = false;
@@ -200,6 +202,10 @@ __global__ void __maxnreg__(WfShape::REGS)
         unsigned char* xslot = xring + (size_t)f * L.x_bytes;
         const C* xs = reinterpret_cast<const C*>(xslot);
         int pending = f < nz ? f : -1;  // layer of the copy in flight into X slot f
+        // Nyquist-row spectra value of component `lane` (even-ky CTA), loaded
+        // one iteration ahead so that its latency is never waited on
+        const bool has_nyq = r == 0 && lane < NC;
+        float snyq_next = (has_nyq && f < nz) ? __ldg(Sk + (size_t)f * S_ROW + lane * JP + J) : 0.f;
         for (int n = f; n < nz; n += FW) {
             const int sf = n % L.df;
             int ok = 1;
@@ -213,8 +219,8 @@ __global__ void __maxnreg__(WfShape::REGS)
                 failed = true;
                 break;
             }
-            float snyq = 0.f;  // Nyquist-row spectra value of component `lane`
-            if (r == 0 && lane < NC) snyq = __ldg(Sk + (size_t)n * s_row + lane * a.jp + J);
+            const float snyq = snyq_next;
+            if (has_nyq && n + FW < nz) snyq_next = __ldg(Sk + (size_t)(n + FW) * S_ROW + lane * JP + J);
             float2 u[32];
 #pragma unroll
             for (int n1 = 0; n1 < 32; ++n1) {
@@ -234,7 +240,7 @@ __global__ void __maxnreg__(WfShape::REGS)
                     bulk_g2s(xslot, Xk + (size_t)(n + FW) * a.ny_pad, L.x_bytes, &xfull[f]);
                     pending = n + FW;
                 }
-                if (n + PF < nz) bulk_prefetch_l2(Sk + (size_t)(n + PF) * s_row, L.s_bytes);
+                if (n + PF < nz) bulk_prefetch_l2(Sk + (size_t)(n + PF) * S_ROW, L.s_bytes);
             }
             C* fb = fring + sf * FS;
             warp_fft1024<false>(u, fb, t2, lane);
@@ -289,7 +295,7 @@ __global__ void __maxnreg__(WfShape::REGS)
         const float* Sq = Sk + q;
         float sv[NC];
 #pragma unroll
-        for (int c = 0; c < NC; ++c) sv[c] = nz > 0 ? __ldg(Sq + c * a.jp) : 0.f;
+        for (int c = 0; c < NC; ++c) sv[c] = nz > 0 ? __ldg(Sq + c * JP) : 0.f;
         for (int n = 0; n < nz; ++n) {
             const int sf = n % L.df;
             if (!ws_wait(&ffull[sf], (uint32_t)((n / L.df) & 1), abort)) {
@@ -308,11 +314,11 @@ __global__ void __maxnreg__(WfShape::REGS)
             }
             mbar_arrive(&fempty[sf]);
             if (n + 1 < nz) {
-                const float* row = Sq + (size_t)(n + 1) * s_row;
+                const float* row = Sq + (size_t)(n + 1) * S_ROW;
 #pragma unroll
-                for (int c = 0; c < NC; ++c) sv[c] = __ldg(row + c * a.jp);
+                for (int c = 0; c < NC; ++c) sv[c] = __ldg(row + c * JP);
             }
-            if ((n % kBlockLayers) == kBlockLayers - 1 || n == nz - 1) {
+            if ((n % WfShape::BLOCK) == WfShape::BLOCK - 1 || n == nz - 1) {
 #pragma unroll
                 for (int c = 0; c < NC; ++c)
 #pragma unroll
@@ -359,7 +365,9 @@ inline WfSmem wf_smem(int ny_pad, int ncomp, int jp, int nc_inst, int max_bytes)
     L.x_bytes = (uint32_t)(ny_pad * sizeof(float2));
     L.s_bytes = (uint32_t)(ncomp * jp * sizeof(float));
     L.f_bytes = (uint32_t)(WfShape::FSLOT * sizeof(float2));
-    if (ny_pad > WfShape::N || nc_inst > WfShape::FWARPS || (L.x_bytes & 15u) || (L.s_bytes & 15u)) return WfSmem{};
+    if (ny_pad > WfShape::N || nc_inst > WfShape::FWARPS || ncomp != nc_inst || jp != WfShape::JP ||
+        (L.x_bytes & 15u) || (L.s_bytes & 15u))
+        return WfSmem{};
     for (int df = 12; df >= WfShape::FWARPS + 1; --df) {
         WfSmem l = L;
         l.df = df;
