@@ -47,7 +47,8 @@ COMPS = 63
 NCOMP = 6
 FALLBACK_HBM_GBS = 6800.0
 PROFILE_SUMMARY = os.path.join(ROOT, "profiles", "forward_columns_grf1024.md")
-KERNEL_SOURCES = ("fft_block.cuh", "spectral.cuh", "spectral_launch.cuh", "col_fwd_f32.cu", "grav_internal.h")
+KERNEL_SOURCES = ("fft_block.cuh", "spectral.cuh", "spectral_ws.cuh", "spectral_wf.cuh", "spectral_launch.cuh",
+                  "async_copy.cuh", "col_fwd_f32.cu", "grav_internal.h")
 
 
 def parse():
@@ -399,7 +400,7 @@ def run_ours(args):
     digest = kernel_digest()
     traffic = profiled_traffic(digest)
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
-                "traffic": traffic, "kernel": "forward_column_kernel (column stage)",
+                "traffic": traffic, "kernel": "forward_column_wf_kernel<6> (column stage)",
                 "algorithmic_bytes": col_alg, "avg_launch_ms": col_ms, "peak_kind": peak_kind,
                 "stage_ms": {k: v / max(1, n_fwd) for k, v in stage_ms.items() if k.startswith("forward")}}
     fwd_alg = spec_b + 4 * nx * ny * nz + 4 * NCOMP * nx * ny
