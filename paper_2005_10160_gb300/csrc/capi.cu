@@ -256,7 +256,7 @@ int run_forward(grav_plan* p, const void* rho, void* out, void* wa, void* wb, in
     grav_plan::TimedCall* tc = batch == 1 ? begin_timed(p, 0) : nullptr;
     mark(tc, 0, s);
     e = launch_row_r2c<R>(p->log_px, (const R*)rho, (size_t)p->ny * p->nx, (size_t)p->nx, p->nx, p->ny, p->nz, wa,
-                          p->ny_pad, p->tw, p->log_t, s, Batch{batch, (size_t)p->nz * p->ny * p->nx, cs});
+                          p->ny_pad, p->tw, p->log_t, s, Batch{batch, (size_t)p->nz * p->ny * p->nx, cs}, p->err_flag);
     if (e != cudaSuccess) return cuda_fail(e, "forward row transform");
     mark(tc, 1, s);
     ColumnArgs a{p->ny, p->ny_pad, p->nz, p->ncomp, p->kx_count, p->jp, p->imag_mask, p->oddv_mask,
@@ -283,7 +283,8 @@ int run_adjoint(grav_plan* p, const void* r, void* grad, void* wa, void* wb, int
     grav_plan::TimedCall* tc = batch == 1 ? begin_timed(p, 1) : nullptr;
     mark(tc, 0, s);
     e = launch_row_r2c<R>(p->log_px, (const R*)r, (size_t)p->ny * p->nx, (size_t)p->nx, p->nx, p->ny, p->ncomp, wb,
-                          p->ny_pad, p->tw, p->log_t, s, Batch{batch, (size_t)p->ncomp * p->ny * p->nx, cs});
+                          p->ny_pad, p->tw, p->log_t, s, Batch{batch, (size_t)p->ncomp * p->ny * p->nx, cs},
+                          p->err_flag);
     if (e != cudaSuccess) return cuda_fail(e, "adjoint row transform");
     mark(tc, 1, s);
     ColumnArgs a{p->ny, p->ny_pad, p->nz, p->ncomp, p->kx_count, p->jp, p->imag_mask, p->oddv_mask,

@@ -13,8 +13,12 @@
 // by Hermitian symmetry, two rows are packed as A + i B, inverse FFT'd, and
 // the first l_out points of each row are kept (the crop back to the
 // stations).
+#include <algorithm>
+
+#include "async_copy.cuh"
 #include "fft_block.cuh"
 #include "grav_internal.h"
+#include "warp_fft.cuh"
 
 namespace grav {
 
@@ -107,6 +111,136 @@ __global__ void __launch_bounds__(NT, 2) row_r2c_kernel(const R* __restrict__ in
     }
 }
 
+// FP32 rows of length P = 2048 with at most 1024 nonzero values (the row
+// stages of every mesh with 513 <= nx <= 1024): the even and the odd outputs
+// are two independent 1024-point transforms,
+//   Z(2k + p) = sum_{x < 1024} z[x] W_2048^(p x) W_1024^(x k),   p = 0, 1,
+// one warp each (warp_fft.cuh).  Conjugate partners k and P - k have the
+// same parity, so splitting Z into the spectra of the two packed real rows
+// only needs one warp's output.
+//
+// Persistent CTAs, two per SM.  A tile is 8 rows of one layer (4 packed
+// sequences, two warps each).  The tile's rows are brought into shared
+// memory by bulk copies (TMA) on an mbarrier; as soon as every warp has read
+// them into registers, the copies of the CTA's next tile are issued, so
+// they land while this tile is transformed and written.  The CTA writes its
+// rows transposed, [kx][o][i], 64 bytes per kx, next to the 64 bytes of the
+// CTA holding the neighbouring tile.  Every wait is bounded.
+constexpr int kRwSeqs = 4;                       // packed sequences per tile
+constexpr int kRwRows = 2 * kRwSeqs;             // rows per tile
+constexpr int kRwThreads = 64 * kRwSeqs;         // two warps per sequence
+constexpr int kRwPitch = 1024;                   // floats per staged row
+// Complex values per warp area: the transpose area plus 2, so that the eight
+// areas start 4 banks apart and the output pass reads them without conflicts.
+constexpr int kRwArea = kWarpFftSlot + 2;
+constexpr size_t kRwAreaOff = (size_t)kRwRows * kRwPitch * sizeof(float);
+constexpr size_t kRwT2Off = kRwAreaOff + (size_t)kRwRows * kRwArea * sizeof(float2);
+constexpr size_t kRwBarOff = kRwT2Off + 1024 * sizeof(float2);
+constexpr size_t kRwSmem = kRwBarOff + 16;
+
+__global__ void __launch_bounds__(kRwThreads, 2)
+    row_r2c_warp_kernel(const float* __restrict__ in, size_t in_ostride, size_t in_istride, int l_in, int I, int O,
+                        float2* __restrict__ out, int i_pad, const float2* __restrict__ tw, int log_t,
+                        size_t in_bstride, size_t out_bstride, int nbatch, int* __restrict__ err) {
+    constexpr int N = 1024, FS = kRwArea;
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    float* sin = reinterpret_cast<float*>(smem_raw);                  // [row][kRwPitch]
+    float2* zs = reinterpret_cast<float2*>(smem_raw + kRwAreaOff);    // per warp: transpose area, then Z_p
+    float2* t2 = reinterpret_cast<float2*>(smem_raw + kRwT2Off);      // W_1024^(k1 n2) at [k1][n2]
+    uint64_t* inb = reinterpret_cast<uint64_t*>(smem_raw + kRwBarOff);
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int rbs = (I + kRwRows - 1) / kRwRows;  // row blocks per layer
+    const long ntiles = (long)nbatch * O * rbs;
+
+    // bulk copies of tile t's rows (thread 0)
+    auto issue = [&](long t) {
+        const int rb = (int)(t % rbs);
+        const long rest = t / rbs;
+        const int o = (int)(rest % O), bz = (int)(rest / O);
+        const int i0 = rb * kRwRows, nrows = min(kRwRows, I - i0);
+        const uint32_t row_bytes = (uint32_t)l_in * sizeof(float);
+        const float* src = in + bz * in_bstride + (size_t)o * in_ostride + (size_t)i0 * in_istride;
+        mbar_arrive_expect_tx(inb, row_bytes * nrows);
+        for (int j = 0; j < nrows; ++j) bulk_g2s(sin + j * kRwPitch, src + (size_t)j * in_istride, row_bytes, inb);
+    };
+
+    if (tid == 0) {
+        mbar_init(inb, 1);
+        fence_mbar_init();
+    }
+    for (int e = tid; e < N; e += kRwThreads) t2[e] = tw[(((e >> 5) * (e & 31)) & (N - 1)) << (log_t - 10)];
+    __syncthreads();
+    if (tid == 0 && blockIdx.x < ntiles) issue(blockIdx.x);
+
+    const int sq = warp >> 1, p = warp & 1;
+    // odd outputs: z[x] W_2048^x with x = 32 n1 + lane, W_2048^x = W_64^n1 W_2048^lane
+    const float2 wl = tw[lane << (log_t - 11)];
+    int it = 0;
+    for (long t = blockIdx.x; t < ntiles; t += gridDim.x, ++it) {
+        const int rb = (int)(t % rbs);
+        const long rest = t / rbs;
+        const int o = (int)(rest % O), bz = (int)(rest / O);
+        const int ib = rb * kRwRows;
+        const bool ok = mbar_wait_bounded(inb, (uint32_t)(it & 1), kWaitLimitNs);
+        const int i0 = ib + 2 * sq;
+        const bool ha = ok && i0 < I, hb = ok && i0 + 1 < I;
+        const float* ra = sin + (2 * sq) * kRwPitch;
+        const float* rbp = ra + kRwPitch;
+        float2 u[32];
+#pragma unroll
+        for (int n1 = 0; n1 < 32; ++n1) {
+            const int x = 32 * n1 + lane;
+            float2 v = make_float2(0.f, 0.f);
+            if (x < l_in) {
+                if (ha) v.x = ra[x];
+                if (hb) v.y = rbp[x];
+                if (p) v = cmul(tw64(v, n1), wl);
+            }
+            u[n1] = v;
+        }
+        if (__syncthreads_or(!ok)) {
+            // a copy did not land in time: record it, let the copy land
+            // (bounded) before the shared memory is released, and leave
+            if (tid == 0) {
+                atomicExch(err, 1);
+                mbar_wait_bounded(inb, (uint32_t)(it & 1), kWaitLimitNs);
+            }
+            return;
+        }
+        // every warp has read the staged rows: bring in the next tile's
+        if (tid == 0 && t + gridDim.x < ntiles) {
+            fence_proxy_async_smem();
+            issue(t + gridDim.x);
+        }
+        float2* zw = zs + warp * FS;
+        warp_fft1024<false>(u, zw, t2, lane);
+#pragma unroll
+        for (int j = 0; j < 32; ++j) zw[lane + 32 * bitrev5(j)] = u[j];
+        __syncthreads();
+
+        // A(kx) = (Z(kx) + conj Z(P - kx)) / 2, B(kx) = (Z(kx) - conj Z(P - kx)) / (2i)
+        float2* outb = out + bz * out_bstride;
+        for (int e = tid; e < kRwSeqs * (N + 1); e += kRwThreads) {
+            const int s = e % kRwSeqs, kx = e / kRwSeqs;
+            const int j0 = ib + 2 * s;
+            if (j0 >= I) continue;
+            const int q = kx & 1, k = kx >> 1;
+            const float2* zp = zs + (2 * s + q) * FS;
+            const float2 zk = zp[k];
+            const float2 zm = cconj(zp[q ? N - 1 - k : (N - k) & (N - 1)]);
+            const float2 A = make_float2(0.5f * (zk.x + zm.x), 0.5f * (zk.y + zm.y));
+            const float2 d = csub(zk, zm);
+            const float2 B = make_float2(0.5f * d.y, -0.5f * d.x);
+            float2* dst = outb + ((size_t)kx * O + o) * i_pad + j0;
+            if (j0 + 1 < I) {
+                *reinterpret_cast<float4*>(dst) = make_float4(A.x, A.y, B.x, B.y);
+            } else {
+                dst[0] = A;
+            }
+        }
+    }
+}
+
 template <typename R, int LOGP, int NSEQ, int NT>
 __global__ void __launch_bounds__(NT, 2) row_c2r_kernel(const typename cplx<R>::type* __restrict__ in0,
                                                       const typename cplx<R>::type* __restrict__ in1, int I, int O,
@@ -180,9 +314,41 @@ cudaError_t r2c_launch(const R* in, size_t in_ostride, size_t in_istride, int l_
     return cudaGetLastError();
 }
 
+// SMs of the current device (cached per device).
+inline int sm_count() {
+    static std::atomic<int> cache[64];
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return 0;
+    int n = cache[dev & 63].load(std::memory_order_relaxed);
+    if (n == 0) {
+        if (cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return 0;
+        cache[dev & 63].store(n, std::memory_order_relaxed);
+    }
+    return n;
+}
+
 template <typename R, int LOGP>
 cudaError_t r2c_impl(const R* in, size_t in_ostride, size_t in_istride, int l_in, int I, int O, void* out, int i_pad,
-                     const void* tw, int log_t, cudaStream_t s, Batch b) {
+                     const void* tw, int log_t, cudaStream_t s, Batch b, int* err) {
+    if constexpr (sizeof(R) == 4 && LOGP == 11) {
+        // 2048-point float rows, at most 1024 nonzero, 16-byte aligned rows:
+        // two warp transforms per row pair, rows staged by bulk copies
+        const int sms = sm_count();
+        const bool fits = err && sms > 0 && l_in <= kRwPitch && l_in % 4 == 0 && in_istride % 4 == 0 &&
+                          in_ostride % 4 == 0 && b.in % 4 == 0 && (reinterpret_cast<uintptr_t>(in) & 15) == 0 &&
+                          i_pad % 2 == 0 && b.out % 2 == 0 && (reinterpret_cast<uintptr_t>(out) & 15) == 0;
+        if (fits) {
+            constexpr auto k = row_r2c_warp_kernel;
+            cudaError_t e = ensure_smem_limit<k>();
+            if (e != cudaSuccess) return e;
+            const long ntiles = (long)b.count * O * ((I + kRwRows - 1) / kRwRows);
+            const int grid = (int)std::min<long>(ntiles, 2L * sms);
+            if (grid == 0) return cudaSuccess;
+            k<<<grid, kRwThreads, kRwSmem, s>>>(in, in_ostride, in_istride, l_in, I, O, (float2*)out, i_pad,
+                                                (const float2*)tw, log_t, b.in, b.out, b.count, err);
+            return cudaGetLastError();
+        }
+    }
     // float rows of at most P/2 values, whole 16-byte vectors, aligned
     if constexpr (sizeof(R) == 4) {
         const bool vec = l_in <= (1 << LOGP) / 2 && l_in % 2 == 0 && in_istride % 2 == 0 && in_ostride % 2 == 0 &&
@@ -214,10 +380,10 @@ cudaError_t c2r_impl(const void* in0, const void* in1, int I, int O, int i_pad, 
 
 template <typename R>
 cudaError_t launch_row_r2c(int log_p, const R* in, size_t in_ostride, size_t in_istride, int l_in, int I, int O,
-                           void* out, int i_pad, const void* tw, int log_t, cudaStream_t s, Batch b) {
+                           void* out, int i_pad, const void* tw, int log_t, cudaStream_t s, Batch b, int* err) {
     switch (log_p) {
 #define CASE(L) \
-    case L: return r2c_impl<R, L>(in, in_ostride, in_istride, l_in, I, O, out, i_pad, tw, log_t, s, b);
+    case L: return r2c_impl<R, L>(in, in_ostride, in_istride, l_in, I, O, out, i_pad, tw, log_t, s, b, err);
         GRAV_LOGP_CASES(CASE)
 #undef CASE
         default: return cudaErrorInvalidValue;
@@ -237,9 +403,9 @@ cudaError_t launch_row_c2r(int log_p, const void* in0, const void* in1, int I, i
 }
 
 template cudaError_t launch_row_r2c<float>(int, const float*, size_t, size_t, int, int, int, void*, int, const void*,
-                                           int, cudaStream_t, Batch);
+                                           int, cudaStream_t, Batch, int*);
 template cudaError_t launch_row_r2c<double>(int, const double*, size_t, size_t, int, int, int, void*, int,
-                                            const void*, int, cudaStream_t, Batch);
+                                            const void*, int, cudaStream_t, Batch, int*);
 template cudaError_t launch_row_c2r<float>(int, const void*, const void*, int, int, int, float*, size_t, int,
                                            const void*, int, cudaStream_t, Batch);
 template cudaError_t launch_row_c2r<double>(int, const void*, const void*, int, int, int, double*, size_t, int,

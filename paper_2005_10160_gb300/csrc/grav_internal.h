@@ -126,10 +126,12 @@ cudaError_t launch_kernel_gen(const Geometry& g, unsigned comps, int n0, int n1,
 // Real rows -> half spectra, written transposed:
 //   in  row (o, i) at in + o * in_ostride + i * in_istride, l_in valid values
 //   out[(kx * O + o) * i_pad + i], kx in [0, P/2]
+// err: device int set to 1 when a bounded wait of a pipelined variant ran out
+// (nullptr: only variants without waits are used).
 template <typename R>
 cudaError_t launch_row_r2c(int log_p, const R* in, size_t in_ostride, size_t in_istride,
                            int l_in, int I, int O, void* out, int i_pad, const void* tw,
-                           int log_t, cudaStream_t s, Batch b = Batch());
+                           int log_t, cudaStream_t s, Batch b = Batch(), int* err = nullptr);
 // Half spectra (the sum of in0 and in1, layout as above) -> real rows:
 //   out row (o, i) at out + (o * I + i) * out_stride, first l_out values.
 template <typename R>

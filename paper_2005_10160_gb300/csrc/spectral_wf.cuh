@@ -26,6 +26,7 @@
 #include "grav_internal.h"
 #include "spectral.cuh"
 #include "spectral_ws.cuh"
+#include "warp_fft.cuh"
 
 namespace grav {
 
@@ -34,7 +35,7 @@ struct WfShape {
     static constexpr int J = 512;          // accumulate threads (16 warps)
     static constexpr int FWARPS = 8;       // FFT warps (2 warpgroups)
     static constexpr int NT = J + 32 * FWARPS;
-    static constexpr int FSLOT = 32 * 33;  // complex values per F slot (transpose area)
+    static constexpr int FSLOT = kWarpFftSlot;  // complex values per F slot (transpose area)
     static constexpr int REGS = 80;        // registers a thread: NT x REGS = 61440
     static constexpr int DX = FWARPS;      // one X slot per FFT warp
     static constexpr int PF = 8;           // spectra prefetch distance (layers)
@@ -47,77 +48,6 @@ struct WfSmem {
     uint32_t x_bytes, s_bytes, f_bytes;
     uint32_t f_off, tw_off, t2_off, cmp_off, bar_off, flag_off, total;
 };
-
-// cos(2 pi j / 32) for any integer j (exact symmetries of the first octant).
-__device__ __forceinline__ float cos32(int j) {
-    const float b[9] = {1.0f,
-                        0.980785280403230449126f,
-                        0.923879532511286756128f,
-                        0.831469612302545237079f,
-                        0.707106781186547524401f,
-                        0.555570233019602224743f,
-                        0.382683432365089771729f,
-                        0.195090322016128267848f,
-                        0.0f};
-    j &= 31;
-    if (j <= 8) return b[j];
-    if (j <= 16) return -b[16 - j];
-    if (j <= 24) return -b[j - 16];
-    return b[32 - j];
-}
-
-// a * W_32^j with W_32 = exp(-+ 2 pi i / 32) (inverse: +); j is a constant
-// after unrolling, so the branches and the cosines fold away.
-template <bool INV> __device__ __forceinline__ float2 tw32(float2 a, int j) {
-    j &= 31;
-    if (j == 0) return a;
-    if (j == 16) return make_float2(-a.x, -a.y);
-    if (j == 8) return INV ? make_float2(-a.y, a.x) : make_float2(a.y, -a.x);
-    if (j == 24) return INV ? make_float2(a.y, -a.x) : make_float2(-a.y, a.x);
-    const float c = cos32(j), s = INV ? cos32(j - 8) : -cos32(j - 8);  // sin(2 pi j/32) = cos(2 pi (j-8)/32)
-    return make_float2(a.x * c - a.y * s, a.x * s + a.y * c);
-}
-
-__host__ __device__ constexpr int bitrev5(int j) {
-    return ((j & 1) << 4) | ((j & 2) << 2) | (j & 4) | ((j & 8) >> 2) | ((j & 16) >> 4);
-}
-
-// 32-point DFT in registers, radix-2 decimation in frequency: natural order
-// in, u[j] = X[bitrev5(j)] out.
-template <bool INV> __device__ __forceinline__ void dft32(float2 (&u)[32]) {
-#pragma unroll
-    for (int h = 16; h >= 1; h >>= 1) {
-#pragma unroll
-        for (int b = 0; b < 32; b += 2 * h) {
-#pragma unroll
-            for (int i = 0; i < h; ++i) {
-                const float2 a = u[b + i], c = u[b + i + h];
-                u[b + i] = make_float2(a.x + c.x, a.y + c.y);
-                u[b + i + h] = tw32<INV>(make_float2(a.x - c.x, a.y - c.y), i * (16 / h));
-            }
-        }
-    }
-}
-
-// 1024-point FFT by one warp.  In: u[n1] = x[32 n1 + lane].  Out: u[j] =
-// X[lane + 32 bitrev5(j)].  tr: the warp's 32 x 33 transpose area; t2[k1 32 +
-// lane] = W_1024^(lane k1).  tr may be overwritten by the caller afterwards.
-template <bool INV>
-__device__ __forceinline__ void warp_fft1024(float2 (&u)[32], float2* tr, const float2* t2, int lane) {
-    dft32<INV>(u);
-#pragma unroll
-    for (int j = 0; j < 32; ++j) {
-        const int k1 = bitrev5(j);
-        float2 w = t2[k1 * 32 + lane];
-        if (INV) w.y = -w.y;
-        tr[k1 * 33 + lane] = cmul(u[j], w);
-    }
-    __syncwarp();
-#pragma unroll
-    for (int n2 = 0; n2 < 32; ++n2) u[n2] = tr[lane * 33 + n2];
-    __syncwarp();
-    dft32<INV>(u);
-}
 
 // CTA-wide barrier (id 1) that the two roles reach from their own code
 // (no .aligned: the arrivals come from different instructions), with an OR

@@ -211,6 +211,36 @@ def test_forward_fp32_wide_columns(gravlib, orc, mesh, comps):
     assert np.all(rel_errors(got32, got64, comps) <= TOL32)
 
 
+# Meshes with 513 <= nx <= 1024: Px = 2048, so the FP32 row stages run the
+# split even/odd warp transforms with staged rows (nx a multiple of 4) or the
+# block transform (nx = 513); ragged row counts included.
+WIDE_ROW_MESHES = [
+    (600, 3, 4, 10.0, 10.0, 10.0, 2.0),
+    (1024, 2, 3, 10.0, 12.0, 10.0, 1.0),
+    (516, 9, 11, 20.0, 15.0, 10.0, 3.0),
+    (513, 7, 2, 20.0, 15.0, 10.0, 3.0),
+]
+
+
+@pytest.mark.parametrize("mesh", WIDE_ROW_MESHES)
+def test_fp32_wide_rows(gravlib, orc, mesh):
+    """FP32 forward and adjoint on 2048-point rows: against the oracle at
+    sampled stations, and against the FP64 spectral path everywhere."""
+    nx, ny, nz = mesh[:3]
+    rng = np.random.default_rng(nx + 7 * ny + nz)
+    rho = rng.uniform(-300, 300, (nz, ny, nx))
+    got32 = run_forward(mesh, ALL7, rho, fp64=False).reshape(7, -1)
+    got64 = run_forward(mesh, ALL7, rho, fp64=True).reshape(7, -1)
+    st = np.unique(np.concatenate([[0, nx * ny - 1, nx // 2], rng.integers(0, nx * ny, 21)])).astype(np.int32)
+    ref = orc.forward(mesh, ALL7, rho, stations=st)
+    assert np.all(rel_errors(got32[:, st], ref, ALL7) <= TOL32)
+    assert np.all(rel_errors(got32, got64, ALL7) <= TOL32)
+    r = rng.normal(size=(7, ny, nx))
+    g32 = run_adjoint(mesh, ALL7, r, fp64=False).reshape(-1)
+    g64 = run_adjoint(mesh, ALL7, r, fp64=True).reshape(-1)
+    assert np.linalg.norm(g32 - g64) <= TOL32 * np.linalg.norm(g64)
+
+
 def test_repeatable_and_stream_ordered(gravlib):
     """Two calls give bit-identical results, on a non-default stream too."""
     mesh, rho = W.small16()
