@@ -430,6 +430,31 @@ def run_ours(args):
            "h2d_bytes_per_step": rho_h.numel() * 4, "d2h_bytes_per_step": out_h.numel() * 4,
            "steps": e_steps, "ms_per_step": e_ms / e_steps}
 
+    # the adjoint G^T r on the same plan (HBM-bound like the forward: it streams
+    # every spectrum once), device-resident N(0,1) residual planes
+    gen = torch.Generator(device=dev)
+    gen.manual_seed(20051016 + 3)
+    r_in = torch.randn((NCOMP, ny, nx), dtype=torch.float32, device=dev, generator=gen)
+    grad = torch.empty((nz, ny, nx), dtype=torch.float32, device=dev)
+    for _ in range(3):
+        plan.adjoint(r_in, grad)
+    torch.cuda.synchronize()
+    capi.grav_plan_set_timing(plan.handle, True)
+    capi.grav_plan_stage_times(plan.handle)  # reset
+    a_steps = max(3, min(args.steps, 20))
+    a0, a1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a0.record(stream)
+    for _ in range(a_steps):
+        plan.adjoint(r_in, grad)
+    a1.record(stream)
+    torch.cuda.synchronize()
+    a_stage, _, n_adj = capi.grav_plan_stage_times(plan.handle)
+    capi.grav_plan_set_timing(plan.handle, False)
+    a_ms = max_over_ranks(world, a0.elapsed_time(a1)) / a_steps
+    adjoint = {"ms_per_step": a_ms, "value": world * pairs / (a_ms / 1000.0), "unit": "pairs/s", "steps": a_steps,
+               "stage_ms": {k: v / max(1, n_adj) for k, v in a_stage.items() if k.startswith("adjoint")}}
+    del r_in, grad
+
     # the all-FP64 spectral path on the same workload, for context
     fp64 = None
     if not args.no_fp64 and rank == 0:
@@ -478,7 +503,7 @@ def run_ours(args):
                        "parallelism": f"replica x{world}", "plan_create_s": plan_s,
                        "forward_algorithmic_bytes": fwd_alg},
             "roofline": roofline, "clocks": clocks, "e2e": e2e, "gpu_launches": 3 * args.steps,
-            "cpu_baseline": cpu, "fp64_path": fp64, "serving": serving,
+            "cpu_baseline": cpu, "fp64_path": fp64, "adjoint": adjoint, "serving": serving,
         }
         print(json.dumps(line), flush=True)
     plan.close()

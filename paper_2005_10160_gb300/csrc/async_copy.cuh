@@ -101,4 +101,22 @@ __device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity
 // Default limit of a pipeline wait: one second.
 constexpr uint64_t kWaitLimitNs = 1000000000ull;
 
+// CTA-wide barrier (id 1) that the roles of a warp-specialised kernel reach
+// from their own code
+// (no .aligned: the arrivals come from different instructions), with an OR
+// of a predicate.
+__device__ __forceinline__ bool cta_sync_or(bool v) {
+    uint32_t out;
+    asm volatile(
+        "{\n\t.reg .pred p, q;\n\t"
+        "setp.ne.u32 p, %1, 0;\n\t"
+        "barrier.red.or.pred q, 1, p;\n\t"
+        "selp.u32 %0, 1, 0, q;\n\t}"
+        : "=r"(out)
+        : "r"((uint32_t)v)
+        : "memory");
+    return out != 0;
+}
+__device__ __forceinline__ void cta_sync() { asm volatile("barrier.sync 1;" ::: "memory"); }
+
 }  // namespace grav

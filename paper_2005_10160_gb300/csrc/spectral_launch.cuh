@@ -2,6 +2,7 @@
 // (transform length, components per thread group).
 #pragma once
 #include "spectral.cuh"
+#include "spectral_adj_wf.cuh"
 #include "spectral_wf.cuh"
 #include "spectral_ws.cuh"
 
@@ -75,11 +76,37 @@ cudaError_t forward_impl(const ColumnArgs& a, const void* X, const R* spec, void
         }                                                                                               \
     }
 
+template <int NC>
+cudaError_t adjoint_wf_launch(const ColumnArgs& a, const AwSmem& L, const void* Xr, const float* spec, void* Z,
+                              const void* tw, int* err, cudaStream_t s, Batch b) {
+    constexpr auto k = adjoint_column_wf_kernel<NC>;
+    cudaError_t e = ensure_smem_limit<k>();
+    if (e != cudaSuccess) return e;
+    k<<<dim3(2 * a.kx_count, b.count), AwShape::NT, L.total, s>>>(a, L, (const float2*)Xr, spec, (float2*)Z,
+                                                                   (const float2*)tw, err, b.in, b.out);
+    return cudaGetLastError();
+}
+
 template <typename R, int LOGN, int CPG>
 cudaError_t adjoint_impl(const ColumnArgs& a, const void* Xr, const R* spec, void* Z, const void* tw, int* err,
                          cudaStream_t s, Batch b) {
     using C = typename cplx<R>::type;
-    (void)err;
+    if constexpr (sizeof(R) == 4 && LOGN == 10) {
+        // 1024-point FP32 columns: one warp per layer transform
+        const AwSmem L = aw_smem(a.ny_pad, a.ncomp, a.jp, a.ncomp, kMaxSmemOptin);
+        if (L.dz != 0 && err) {
+            switch (a.ncomp) {
+                case 1: return adjoint_wf_launch<1>(a, L, Xr, spec, Z, tw, err, s, b);
+                case 2: return adjoint_wf_launch<2>(a, L, Xr, spec, Z, tw, err, s, b);
+                case 3: return adjoint_wf_launch<3>(a, L, Xr, spec, Z, tw, err, s, b);
+                case 4: return adjoint_wf_launch<4>(a, L, Xr, spec, Z, tw, err, s, b);
+                case 5: return adjoint_wf_launch<5>(a, L, Xr, spec, Z, tw, err, s, b);
+                case 6: return adjoint_wf_launch<6>(a, L, Xr, spec, Z, tw, err, s, b);
+                case 7: return adjoint_wf_launch<7>(a, L, Xr, spec, Z, tw, err, s, b);
+                default: break;
+            }
+        }
+    }
     constexpr auto k = adjoint_column_kernel<R, LOGN, CPG>;
     const size_t smem = column_smem_bytes<R>(LOGN);
     cudaError_t e = ensure_smem_limit<k>();

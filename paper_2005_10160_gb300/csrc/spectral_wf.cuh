@@ -49,23 +49,6 @@ struct WfSmem {
     uint32_t f_off, tw_off, t2_off, cmp_off, bar_off, flag_off, total;
 };
 
-// CTA-wide barrier (id 1) that the two roles reach from their own code
-// (no .aligned: the arrivals come from different instructions), with an OR
-// of a predicate.
-__device__ __forceinline__ bool cta_sync_or(bool v) {
-    uint32_t out;
-    asm volatile(
-        "{\n\t.reg .pred p, q;\n\t"
-        "setp.ne.u32 p, %1, 0;\n\t"
-        "barrier.red.or.pred q, 1, p;\n\t"
-        "selp.u32 %0, 1, 0, q;\n\t}"
-        : "=r"(out)
-        : "r"((uint32_t)v)
-        : "memory");
-    return out != 0;
-}
-__device__ __forceinline__ void cta_sync() { asm volatile("barrier.sync 1;" ::: "memory"); }
-
 template <int NC>
 __global__ void __maxnreg__(WfShape::REGS)
     forward_column_wf_kernel(ColumnArgs a, WfSmem L, const float2* __restrict__ X, const float* __restrict__ spec,

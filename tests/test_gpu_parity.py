@@ -197,7 +197,8 @@ WIDE_MESHES = [
 @pytest.mark.parametrize("comps", [ALL7, 0x3F, capi.GRAV_GZ, capi.GRAV_GXY | capi.GRAV_GYZ])
 def test_forward_fp32_wide_columns(gravlib, orc, mesh, comps):
     """FP32 forward on 2048-point columns: against the oracle at sampled
-    stations, and against the FP64 spectral path at every station."""
+    stations, and against the FP64 spectral path at every station; the FP32
+    adjoint against the FP64 adjoint at every cell."""
     nx, ny, nz = mesh[:3]
     rng = np.random.default_rng(nx * 1000 + ny + nz)
     rho = rng.uniform(-300, 300, (nz, ny, nx))
@@ -209,6 +210,11 @@ def test_forward_fp32_wide_columns(gravlib, orc, mesh, comps):
     assert np.all(rel_errors(got32[:, st], ref, comps) <= TOL32)
     assert np.all(rel_errors(got64[:, st], ref, comps) <= TOL64)
     assert np.all(rel_errors(got32, got64, comps) <= TOL32)
+    # the adjoint on the same columns: FP32 against the FP64 spectral path
+    r = rng.normal(size=(len(capi.comp_list(comps)), ny, nx))
+    g32 = run_adjoint(mesh, comps, r, fp64=False).reshape(-1)
+    g64 = run_adjoint(mesh, comps, r, fp64=True).reshape(-1)
+    assert np.linalg.norm(g32 - g64) <= TOL32 * np.linalg.norm(g64)
 
 
 # Meshes with 513 <= nx <= 1024: Px = 2048, so the FP32 row stages run the
