@@ -289,13 +289,22 @@ int run_adjoint(grav_plan* p, const void* r, void* grad, void* wa, void* wb, int
     mark(tc, 1, s);
     ColumnArgs a{p->ny, p->ny_pad, p->nz, p->ncomp, p->kx_count, p->jp, p->imag_mask, p->oddv_mask,
                  p->log_t - (p->log_py - 1), p->log_t - p->log_py};
+    // FP32 2048 x 2048 plans: tile-major column output, read back by whole tiles
+    if constexpr (sizeof(R) == 4) a.z_tiled = adjoint_tiled_ok(p->log_py - 1, p->log_px, p->nx, a) ? 1 : 0;
     e = launch_adjoint_columns<R>(p->log_py - 1, a, wb, (const R*)p->spec, wa, p->tw, p->err_flag, s,
                                   Batch{batch, cs, cs});
     if (e != cudaSuccess) return cuda_fail(e, "adjoint column stage");
     mark(tc, 2, s);
     const size_t half = (size_t)p->kx_count * p->nz * p->ny_pad * 2 * sizeof(R);
-    e = launch_row_c2r<R>(p->log_px, wa, (const unsigned char*)wa + half, p->ny, p->nz, p->ny_pad, (R*)grad,
-                          (size_t)p->nx, p->nx, p->tw, p->log_t, s, Batch{batch, cs, (size_t)p->nz * p->ny * p->nx});
+    if (a.z_tiled) {
+        e = launch_row_c2r_tiled(wa, (const unsigned char*)wa + half, p->ny, p->nz, p->kx_count, (float*)grad,
+                                 (size_t)p->nx, p->nx, p->tw, p->log_t, s,
+                                 Batch{batch, cs, (size_t)p->nz * p->ny * p->nx}, p->err_flag);
+    } else {
+        e = launch_row_c2r<R>(p->log_px, wa, (const unsigned char*)wa + half, p->ny, p->nz, p->ny_pad, (R*)grad,
+                              (size_t)p->nx, p->nx, p->tw, p->log_t, s,
+                              Batch{batch, cs, (size_t)p->nz * p->ny * p->nx});
+    }
     if (e != cudaSuccess) return cuda_fail(e, "adjoint inverse row transform");
     mark(tc, 3, s);
     return GRAV_OK;

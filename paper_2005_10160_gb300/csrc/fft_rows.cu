@@ -126,6 +126,8 @@ __global__ void __launch_bounds__(NT, 2) row_r2c_kernel(const R* __restrict__ in
 // they land while this tile is transformed and written.  The CTA writes its
 // rows transposed, [kx][o][i], 64 bytes per kx, next to the 64 bytes of the
 // CTA holding the neighbouring tile.  Every wait is bounded.
+__host__ __device__ inline int ny_blocks(int ny) { return (ny + 7) / 8; }
+
 constexpr int kRwSeqs = 4;                       // packed sequences per tile
 constexpr int kRwRows = 2 * kRwSeqs;             // rows per tile
 constexpr int kRwThreads = 64 * kRwSeqs;         // two warps per sequence
@@ -236,6 +238,123 @@ __global__ void __launch_bounds__(kRwThreads, 2)
                 *reinterpret_cast<float4*>(dst) = make_float4(A.x, A.y, B.x, B.y);
             } else {
                 dst[0] = A;
+            }
+        }
+    }
+}
+
+// Adjoint inverse rows, FP32, P = 2048, from the tiled column output
+// in_r[n][y / 8][kx][8] of both ky parities (summed here); within a kx run,
+// row pair j (rows 2j, 2j + 1 of the tile) is at 16-byte position
+// (j + kx / 2) % 4.  Only the
+// first 1024 outputs of each length-2048 inverse transform are kept, so the
+// transform is split by output parity (decimation in frequency):
+//   z[2m]     = sum_{k < 1024} (Z(k) + Z(k + 1024))            W_1024^(-m k)
+//   z[2m + 1] = sum_{k < 1024} (Z(k) - Z(k + 1024)) W_2048^(-k) W_1024^(-m k)
+// one 1024-point warp transform each (warp_fft1024), with Z(k) = A(k) + i B(k)
+// for the packed rows a, b and Z(k) for k > 1024 from Hermitian symmetry.
+// Persistent CTAs, one per SM.  A tile is 8 rows of one layer: two
+// contiguous runs (one per parity) brought in by bulk copies on an mbarrier;
+// once every warp has read its inputs into registers, the next tile's
+// copies are issued.  Warp w handles rows 2 (w / 2), 2 (w / 2) + 1 and
+// output parity w % 2, and stores its outputs straight to the rows.
+constexpr int kCtRows = 8;                         // rows per tile
+constexpr int kCtThreads = 32 * kCtRows;           // two warps per packed row pair
+constexpr int kCtKx = 1025;                        // P / 2 + 1
+constexpr size_t kCtHalf = (size_t)kCtKx * kCtRows * sizeof(float2);  // bytes of one parity's tile
+constexpr size_t kCtAreaOff = 2 * kCtHalf;
+constexpr size_t kCtT2Off = kCtAreaOff + (size_t)kCtRows * kWarpFftSlot * sizeof(float2);
+constexpr size_t kCtBarOff = kCtT2Off + 1024 * sizeof(float2);
+constexpr size_t kCtSmem = kCtBarOff + 16;
+
+__global__ void __launch_bounds__(kCtThreads, 1)
+    row_c2r_tiled_kernel(const float2* __restrict__ in0, const float2* __restrict__ in1, int ny, int nz,
+                         float* __restrict__ out, size_t out_stride, int l_out, const float2* __restrict__ tw,
+                         int log_t, size_t in_bstride, size_t out_bstride, int nbatch, int* __restrict__ err) {
+    constexpr int N = 1024;
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    const float2* t0 = reinterpret_cast<const float2*>(smem_raw);            // [kx][8] parity 0
+    const float2* t1 = reinterpret_cast<const float2*>(smem_raw + kCtHalf);  // [kx][8] parity 1
+    float2* areas = reinterpret_cast<float2*>(smem_raw + kCtAreaOff);
+    float2* t2 = reinterpret_cast<float2*>(smem_raw + kCtT2Off);
+    uint64_t* inb = reinterpret_cast<uint64_t*>(smem_raw + kCtBarOff);
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int ybs = ny_blocks(ny);
+    const long ntiles = (long)nbatch * nz * ybs;
+
+    auto issue = [&](long t) {  // thread 0: both parities' runs of tile t
+        const long bz = t / ((long)nz * ybs), rest = t - bz * nz * ybs;  // rest = n * ybs + yb
+        const size_t off = (size_t)rest * kCtKx * kCtRows;
+        mbar_arrive_expect_tx(inb, (uint32_t)(2 * kCtHalf));
+        bulk_g2s(smem_raw, in0 + bz * in_bstride + off, (uint32_t)kCtHalf, inb);
+        bulk_g2s(smem_raw + kCtHalf, in1 + bz * in_bstride + off, (uint32_t)kCtHalf, inb);
+    };
+
+    if (tid == 0) {
+        mbar_init(inb, 1);
+        fence_mbar_init();
+    }
+    for (int e = tid; e < N; e += kCtThreads) t2[e] = tw[(((e >> 5) * (e & 31)) & (N - 1)) << (log_t - 10)];
+    __syncthreads();
+    if (tid == 0 && blockIdx.x < ntiles) issue(blockIdx.x);
+
+    const int sq = warp >> 1, p = warp & 1;
+    // odd outputs: W_2048^(-k) with k = 32 n1 + lane = W_64^(-n1) W_2048^(-lane)
+    const float2 wl = cconj(tw[lane << (log_t - 11)]);
+    int it = 0;
+    for (long t = blockIdx.x; t < ntiles; t += gridDim.x, ++it) {
+        const long bz = t / ((long)nz * ybs), rest = t - bz * nz * ybs;
+        const int n = (int)(rest / ybs), yb = (int)(rest - (long)n * ybs);
+        const int ya = yb * kCtRows + 2 * sq;
+        const bool ok = mbar_wait_bounded(inb, (uint32_t)(it & 1), kWaitLimitNs);
+        const bool ha = ok && ya < ny, hb = ok && ya + 1 < ny;
+        // packed spectrum Z(k) = A(k) + i B(k) of rows ya, ya + 1 at kx (both parities summed)
+        auto zk = [&](int kx) {
+            const int pos = 2 * ((sq + (kx >> 1)) & 3);  // row pair sq's 16-byte position in the run
+            const float4 v0 = *reinterpret_cast<const float4*>(t0 + kx * kCtRows + pos);
+            const float4 v1 = *reinterpret_cast<const float4*>(t1 + kx * kCtRows + pos);
+            float2 A = make_float2(v0.x + v1.x, v0.y + v1.y), B = make_float2(v0.z + v1.z, v0.w + v1.w);
+            if (!ha) A = make_float2(0.f, 0.f);
+            if (!hb) B = make_float2(0.f, 0.f);
+            if (kx == 0 || kx == kCtKx - 1) A.y = B.y = 0.f;  // real DC and Nyquist
+            return make_float4(A.x, A.y, B.x, B.y);
+        };
+        float2 u[32];
+#pragma unroll
+        for (int n1 = 0; n1 < 32; ++n1) {
+            const int k = 32 * n1 + lane;
+            const float4 a1 = zk(k);
+            const float2 z1 = make_float2(a1.x - a1.w, a1.y + a1.z);  // A + i B
+            const float4 a2 = zk(N - k);                                // k = 0: the Nyquist bin itself
+            // Z(k + 1024) = conj A(1024 - k) + i conj B(1024 - k) (k > 0), A + i B at the Nyquist bin (k = 0)
+            const float2 z2 = k ? make_float2(a2.x + a2.w, a2.z - a2.y) : make_float2(a2.x - a2.w, a2.y + a2.z);
+            float2 v = p ? make_float2(z1.x - z2.x, z1.y - z2.y) : make_float2(z1.x + z2.x, z1.y + z2.y);
+            if (p) v = cmul(tw64(v, -n1), wl);
+            u[n1] = v;
+        }
+        if (__syncthreads_or(!ok)) {
+            // a copy did not land in time: record it, let the copy land
+            // (bounded) before the shared memory is released, and leave
+            if (tid == 0) {
+                atomicExch(err, 1);
+                mbar_wait_bounded(inb, (uint32_t)(it & 1), kWaitLimitNs);
+            }
+            return;
+        }
+        if (tid == 0 && t + gridDim.x < ntiles) {
+            fence_proxy_async_smem();
+            issue(t + gridDim.x);
+        }
+        warp_fft1024<true>(u, areas + warp * kWarpFftSlot, t2, lane);
+        // u[j] = z[2 m + p], m = lane + 32 bitrev5(j)
+        float* oa = out + bz * out_bstride + ((size_t)n * ny + ya) * out_stride;
+        float* ob = oa + out_stride;
+#pragma unroll
+        for (int j = 0; j < 32; ++j) {
+            const int x = 2 * (lane + 32 * bitrev5(j)) + p;
+            if (x < l_out) {
+                if (ya < ny) oa[x] = u[j].x;
+                if (ya + 1 < ny) ob[x] = u[j].y;
             }
         }
     }
@@ -400,6 +519,25 @@ cudaError_t launch_row_c2r(int log_p, const void* in0, const void* in1, int I, i
 #undef CASE
         default: return cudaErrorInvalidValue;
     }
+}
+
+cudaError_t launch_row_c2r_tiled(const void* in0, const void* in1, int ny, int nz, int kx_count, float* out,
+                                 size_t out_stride, int l_out, const void* tw, int log_t, cudaStream_t s, Batch b,
+                                 int* err) {
+    if (kx_count != kCtKx || l_out > 1024 || !err || (reinterpret_cast<uintptr_t>(in0) & 15) ||
+        (reinterpret_cast<uintptr_t>(in1) & 15) || (b.in * sizeof(float2)) % 16)
+        return cudaErrorInvalidValue;
+    const int sms = sm_count();
+    if (sms <= 0) return cudaErrorInvalidValue;
+    constexpr auto k = row_c2r_tiled_kernel;
+    cudaError_t e = ensure_smem_limit<k>();
+    if (e != cudaSuccess) return e;
+    const long ntiles = (long)b.count * nz * ny_blocks(ny);
+    const int grid = (int)std::min<long>(ntiles, sms);
+    if (grid == 0) return cudaSuccess;
+    k<<<grid, kCtThreads, kCtSmem, s>>>((const float2*)in0, (const float2*)in1, ny, nz, out, out_stride, l_out,
+                                        (const float2*)tw, log_t, b.in, b.out, b.count, err);
+    return cudaGetLastError();
 }
 
 template cudaError_t launch_row_r2c<float>(int, const float*, size_t, size_t, int, int, int, void*, int, const void*,

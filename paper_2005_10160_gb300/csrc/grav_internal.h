@@ -48,6 +48,10 @@ struct ColumnArgs {
     unsigned oddv_mask;  // bit s: component slot s is odd in y
     int tw_shift_n;      // log2(T / N) for the half-length column transform
     int tw_shift_p;      // log2(T / Py) for the parity fold twiddles
+    int z_tiled;         // adjoint output layout: 0 = Z[r][kx][n][y] (row stride ny_pad),
+                         // 1 = Z[r][n][y / 8][kx][8], row pair (y % 8) / 2 at 16-byte position
+                         // ((y % 8) / 2 + kx / 2) % 4 of the run (ny_pad a multiple of 8;
+                         // see launch_row_c2r_tiled)
 };
 
 }  // namespace grav
@@ -138,6 +142,18 @@ template <typename R>
 cudaError_t launch_row_c2r(int log_p, const void* in0, const void* in1, int I, int O, int i_pad,
                            R* out, size_t out_stride, int l_out, const void* tw, int log_t,
                            cudaStream_t s, Batch b = Batch());
+
+// Adjoint inverse rows from the tiled column output (ColumnArgs::z_tiled):
+// in_r[n][y / 8][kx][8] (swizzled as described there) for r = 0, 1 (in1 = in0 + one half), summed, kx
+// in [0, 1024]; out row (n, y) at out + (n * ny + y) * out_stride, first
+// l_out <= 1024 values.  FP32, P = 2048.  err as for the column kernels.
+cudaError_t launch_row_c2r_tiled(const void* in0, const void* in1, int ny, int nz, int kx_count, float* out,
+                                 size_t out_stride, int l_out, const void* tw, int log_t, cudaStream_t s,
+                                 Batch b, int* err);
+// Whether the FP32 adjoint of a plan with these sizes runs the tiled column
+// output and launch_row_c2r_tiled (log_n: column transform length, log_px:
+// row transform length).
+bool adjoint_tiled_ok(int log_n, int log_px, int nx, const ColumnArgs& a);
 
 // ---- column kernels (spectral.cuh, col_*.cu) ----
 // err: device int set to 1 when a pipeline wait ran out (the kernel then

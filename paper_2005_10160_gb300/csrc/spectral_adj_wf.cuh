@@ -179,14 +179,33 @@ __global__ void __maxnreg__(AwShape::REGS)
             __syncwarp();
             warp_fft1024<true>(u, zb, t2, lane);
             mbar_arrive(&zempty[sz]);  // this lane is done with the slot (transposes included)
-            C* dst = Z + ((size_t)(r * a.kx_count + kx) * nz + n) * a.ny_pad;
+            if (a.z_tiled) {
+                // Z[r][n][y / 8][kx][8]: eight lanes fill one 64-byte run; row pair
+                // (y % 8) / 2 sits at 16-byte position ((y % 8) / 2 + kx / 2) % 4 of the
+                // run, so that the reader's 16-byte loads of consecutive kx fall in
+                // distinct shared-memory banks
+                C* dst = Z + ((size_t)(r * nz + n) * (a.ny_pad >> 3) * a.kx_count + kx) * 8;
+                const int rot = kx >> 1;
 #pragma unroll
-            for (int j = 0; j < 32; ++j) {
-                const int y = lane + 32 * bitrev5(j);
-                if (y < ny) {
-                    C v = u[j];
-                    if (r) v = cmul(v, cconj(tws[y]));
-                    dst[y] = v;
+                for (int j = 0; j < 32; ++j) {
+                    const int y = lane + 32 * bitrev5(j);
+                    if (y < ny) {
+                        C v = u[j];
+                        if (r) v = cmul(v, cconj(tws[y]));
+                        const int pos = 2 * ((((y & 7) >> 1) + rot) & 3) + (y & 1);
+                        dst[(size_t)(y >> 3) * a.kx_count * 8 + pos] = v;
+                    }
+                }
+            } else {
+                C* dst = Z + ((size_t)(r * a.kx_count + kx) * nz + n) * a.ny_pad;
+#pragma unroll
+                for (int j = 0; j < 32; ++j) {
+                    const int y = lane + 32 * bitrev5(j);
+                    if (y < ny) {
+                        C v = u[j];
+                        if (r) v = cmul(v, cconj(tws[y]));
+                        dst[y] = v;
+                    }
                 }
             }
         }

@@ -247,6 +247,32 @@ def test_fp32_wide_rows(gravlib, orc, mesh):
     assert np.linalg.norm(g32 - g64) <= TOL32 * np.linalg.norm(g64)
 
 
+# Both axes 513..1024 (Px = Py = 2048) with ny a multiple of 4 and 8:
+# the FP32 adjoint writes its column output tile-major and reads it back
+# by whole tiles (the last tile ragged for ny = 517).
+WIDE_BOTH_MESHES = [
+    (520, 600, 5, 20.0, 20.0, 10.0, 4.0),
+    (600, 517, 3, 10.0, 10.0, 10.0, 2.0),
+]
+
+
+@pytest.mark.parametrize("mesh", WIDE_BOTH_MESHES)
+def test_fp32_adjoint_wide_both(gravlib, mesh):
+    """FP32 adjoint against the FP64 adjoint at every cell, and the FP32
+    dot-product identity <G x, y> = <x, G^T y>."""
+    nx, ny, nz = mesh[:3]
+    rng = np.random.default_rng(nx * 3 + ny)
+    r = rng.normal(size=(7, ny, nx))
+    g32 = run_adjoint(mesh, ALL7, r, fp64=False)
+    g64 = run_adjoint(mesh, ALL7, r, fp64=True)
+    assert np.linalg.norm((g32 - g64).ravel()) <= TOL32 * np.linalg.norm(g64.ravel())
+    x = rng.uniform(-300, 300, (nz, ny, nx))
+    gx = run_forward(mesh, ALL7, x, fp64=False).astype(np.float64)
+    lhs = float(np.dot(gx.ravel(), r.ravel()))
+    rhs = float(np.dot(x.ravel(), g32.astype(np.float64).ravel()))
+    assert abs(lhs - rhs) <= 1e-5 * np.linalg.norm(gx.ravel()) * np.linalg.norm(r.ravel())
+
+
 def test_repeatable_and_stream_ordered(gravlib):
     """Two calls give bit-identical results, on a non-default stream too."""
     mesh, rho = W.small16()
