@@ -12,6 +12,7 @@ import torch
 
 from paper_2005_10160_gb300 import capi, workloads as W
 from paper_2005_10160_gb300.batch import BatchRunner
+from paper_2005_10160_gb300.pipeline import HostPipeline
 from paper_2005_10160_gb300.plan import Plan
 from paper_2005_10160_gb300.server import Server
 
@@ -140,3 +141,21 @@ def test_batch_runner_matches_single_calls(gravlib, mesh):
         for i in range(3):
             assert torch.equal(y[i], plan.forward(x[i].contiguous()))
             assert torch.equal(g[i], plan.adjoint(r[i].contiguous()))
+
+
+def test_host_pipeline_matches_plain_calls(gravlib):
+    """HostPipeline (two lanes, host-resident pinned buffers) gives for every
+    request exactly what a plain forward on device buffers gives."""
+    mesh = W.Mesh(520, 528, 3, 20.0, 20.0, 10.0, 5.0)
+    rng = np.random.default_rng(9)
+    with Plan(mesh, capi.GRAV_ALL6) as plan:
+        pipe = HostPipeline(plan, lanes=2)
+        rhos = [torch.as_tensor(rng.uniform(-300, 300, (mesh.nz, mesh.ny, mesh.nx)), dtype=torch.float32).pin_memory()
+                for _ in range(5)]
+        outs = [torch.empty((6, mesh.ny, mesh.nx), dtype=torch.float32).pin_memory() for _ in rhos]
+        for rh, oh in zip(rhos, outs):
+            pipe.forward(rh, oh)
+        pipe.synchronize()
+        for rh, oh in zip(rhos, outs):
+            ref = plan.forward(rh.cuda()).cpu()
+            assert torch.equal(oh, ref)
