@@ -8,7 +8,9 @@
 // in registers (warp_fft1024); thread q of warps 0-15 keeps both bins of
 // mirror pair q of every component in registers.  Then, layer by layer, the
 // combine threads form the layer's spectrum from their bins and the layer's
-// spectra values (read from global memory one layer ahead) and write it
+// spectra values (read from global memory one layer ahead, after a bulk L2
+// prefetch eight layers ahead: the combine threads run ahead of the
+// transforms, so a load from DRAM would stall every layer) and write it
 // into a ring slot; FFT warp f inverse-transforms layers f, f + 8, ... from
 // the slot (which is also its transpose area) and writes the rows y < ny.
 // The combine threads run up to (ring depth - 8) layers ahead of the
@@ -30,6 +32,7 @@ struct AwShape {
     static constexpr int SLOT = kWarpFftSlot;
     static constexpr int REGS = 80;
     static constexpr int JP = 516;    // spectra row pitch: J + 1 rounded up to 4
+    static constexpr int PF = 8;      // spectra prefetch distance into L2 (layers)
 };
 
 struct AwSmem {
@@ -124,9 +127,15 @@ __global__ void __maxnreg__(AwShape::REGS)
                 se[c] = nyq ? __ldg(row + c * JP + (J - q)) : 0.f;
             }
         };
+        // spectra of the first PF layers into L2 (thread 0), then one layer
+        // more each iteration, so that the one-layer-ahead loads hit L2
+        constexpr int PF = AwShape::PF;
+        if (q == 0)
+            for (int n = 0; n < PF && n < nz; ++n) bulk_prefetch_l2(Sk + (size_t)n * S_ROW, S_ROW * sizeof(float));
         if (nz > 0) load(0);
         for (int n = 0; n < nz; ++n) {
             const int sz = n % L.dz;
+            if (q == 0 && n + PF < nz) bulk_prefetch_l2(Sk + (size_t)(n + PF) * S_ROW, S_ROW * sizeof(float));
             if (n >= L.dz && !ws_wait(&zempty[sz], (uint32_t)((n / L.dz - 1) & 1), abort)) {
                 failed = true;
                 break;
