@@ -220,24 +220,31 @@ __global__ void __launch_bounds__(kRwThreads, 2)
         for (int j = 0; j < 32; ++j) zw[lane + 32 * bitrev5(j)] = u[j];
         __syncthreads();
 
-        // A(kx) = (Z(kx) + conj Z(P - kx)) / 2, B(kx) = (Z(kx) - conj Z(P - kx)) / (2i)
-        float2* outb = out + bz * out_bstride;
-        for (int e = tid; e < kRwSeqs * (N + 1); e += kRwThreads) {
-            const int s = e % kRwSeqs, kx = e / kRwSeqs;
+        // A(kx) = (Z(kx) + conj Z(P - kx)) / 2, B(kx) = (Z(kx) - conj Z(P - kx)) / (2i).
+        // Thread t writes packed sequence t % 4 for kx = t / 4, t / 4 + 64, ...: its
+        // row pair and output parity stay fixed (a warp writes 8 kx x 64 bytes).
+        {
+            constexpr int KSTEP = kRwThreads / kRwSeqs;  // 64, even: the parity of kx stays fixed
+            const int s = tid % kRwSeqs, kx0 = tid / kRwSeqs, q = kx0 & 1;
             const int j0 = ib + 2 * s;
-            if (j0 >= I) continue;
-            const int q = kx & 1, k = kx >> 1;
-            const float2* zp = zs + (2 * s + q) * FS;
-            const float2 zk = zp[k];
-            const float2 zm = cconj(zp[q ? N - 1 - k : (N - k) & (N - 1)]);
-            const float2 A = make_float2(0.5f * (zk.x + zm.x), 0.5f * (zk.y + zm.y));
-            const float2 d = csub(zk, zm);
-            const float2 B = make_float2(0.5f * d.y, -0.5f * d.x);
-            float2* dst = outb + ((size_t)kx * O + o) * i_pad + j0;
-            if (j0 + 1 < I) {
-                *reinterpret_cast<float4*>(dst) = make_float4(A.x, A.y, B.x, B.y);
-            } else {
-                dst[0] = A;
+            if (j0 < I) {
+                const float2* zp = zs + (2 * s + q) * FS;
+                const bool pair = j0 + 1 < I;
+                const size_t dstep = (size_t)KSTEP * O * i_pad;
+                float2* dst = out + bz * out_bstride + ((size_t)kx0 * O + o) * i_pad + j0;
+                for (int kx = kx0; kx <= N; kx += KSTEP, dst += dstep) {
+                    const int k = kx >> 1;
+                    const float2 zk = zp[k];
+                    const float2 zm = cconj(zp[q ? N - 1 - k : (N - k) & (N - 1)]);
+                    const float2 A = make_float2(0.5f * (zk.x + zm.x), 0.5f * (zk.y + zm.y));
+                    const float2 d = csub(zk, zm);
+                    const float2 B = make_float2(0.5f * d.y, -0.5f * d.x);
+                    if (pair) {
+                        *reinterpret_cast<float4*>(dst) = make_float4(A.x, A.y, B.x, B.y);
+                    } else {
+                        dst[0] = A;
+                    }
+                }
             }
         }
     }

@@ -40,7 +40,7 @@ struct WfShape {
     static constexpr int DX = FWARPS;      // one X slot per FFT warp
     static constexpr int PF = 8;           // spectra prefetch distance (layers)
     static constexpr int JP = 516;         // spectra row pitch: J + 1 rounded up to 4
-    static constexpr int BLOCK = 16;       // layers per compensated block
+    static constexpr int BLOCK = 32;       // layers per compensated block
 };
 
 struct WfSmem {
