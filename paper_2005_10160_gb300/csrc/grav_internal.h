@@ -1,5 +1,6 @@
 // Internal plan structure and kernel launchers of the GB300 forward library.
 #pragma once
+#include <cuda.h>
 #include <cuda_runtime.h>
 #include <stddef.h>
 #include <stdint.h>
@@ -154,6 +155,12 @@ cudaError_t launch_row_c2r_tiled(const void* in0, const void* in1, int ny, int n
 // output and launch_row_c2r_tiled (log_n: column transform length, log_px:
 // row transform length).
 bool adjoint_tiled_ok(int log_n, int log_px, int nx, const ColumnArgs& a);
+// Tensor map of the tiled adjoint column output Z (see ColumnArgs::z_tiled)
+// for tensor stores of one layer's column: 8-byte elements, dims (8, kx,
+// y / 8, 2 nz, batch), box (8, 1, 128, 1, 1).  z_bstride: complex elements
+// between the requests of a batched call.
+cudaError_t make_ztile_map(CUtensorMap* map, void* Z, int nz, int ny_pad, int kx_count, int batch,
+                           size_t z_bstride);
 
 // ---- column kernels (spectral.cuh, col_*.cu) ----
 // err: device int set to 1 when a pipeline wait ran out (the kernel then

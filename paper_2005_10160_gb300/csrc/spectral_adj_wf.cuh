@@ -44,7 +44,7 @@ template <int NC>
 __global__ void __maxnreg__(AwShape::REGS)
     adjoint_column_wf_kernel(ColumnArgs a, AwSmem L, const float2* __restrict__ Xr, const float* __restrict__ spec,
                              float2* __restrict__ Z, const float2* __restrict__ tw, int* __restrict__ err,
-                             size_t x_bstride, size_t z_bstride) {
+                             size_t x_bstride, size_t z_bstride, const __grid_constant__ CUtensorMap zmap) {
     using C = float2;
     constexpr int N = AwShape::N, J = AwShape::J, FW = AwShape::FWARPS, NT = AwShape::NT;
     constexpr int FS = AwShape::SLOT, JP = AwShape::JP, S_ROW = NC * JP;
@@ -187,25 +187,29 @@ __global__ void __maxnreg__(AwShape::REGS)
             for (int n1 = 0; n1 < 32; ++n1) u[n1] = zb[32 * n1 + lane];
             __syncwarp();
             warp_fft1024<true>(u, zb, t2, lane);
-            mbar_arrive(&zempty[sz]);  // this lane is done with the slot (transposes included)
             if (a.z_tiled) {
-                // Z[r][n][y / 8][kx][8]: eight lanes fill one 64-byte run; row pair
-                // (y % 8) / 2 sits at 16-byte position ((y % 8) / 2 + kx / 2) % 4 of the
-                // run, so that the reader's 16-byte loads of consecutive kx fall in
-                // distinct shared-memory banks
-                C* dst = Z + ((size_t)(r * nz + n) * (a.ny_pad >> 3) * a.kx_count + kx) * 8;
-                const int rot = kx >> 1;
+                // Stage the layer in the slot in the order of its tiles, Z[.][.][y / 8][kx][8]
+                // with row pair (y % 8) / 2 at 16-byte position ((y % 8) / 2 + kx / 2) % 4,
+                // and write it with one tensor store (zmap: 8 x kx x y/8 x (r, n) x request).
+                const int pos = 2 * ((((lane & 7) >> 1) + (kx >> 1)) & 3) + (lane & 1);  // y % 8 = lane % 8
 #pragma unroll
                 for (int j = 0; j < 32; ++j) {
                     const int y = lane + 32 * bitrev5(j);
-                    if (y < ny) {
-                        C v = u[j];
-                        if (r) v = cmul(v, cconj(tws[y]));
-                        const int pos = 2 * ((((y & 7) >> 1) + rot) & 3) + (y & 1);
-                        dst[(size_t)(y >> 3) * a.kx_count * 8 + pos] = v;
-                    }
+                    C v = u[j];
+                    if (r) v = cmul(v, cconj(tws[y]));
+                    zb[(y & ~7) + pos] = v;
                 }
+                fence_proxy_async_smem();  // these writes before the tensor store's reads
+                __syncwarp();
+                if (lane == 0) {
+                    tma_store_5d(&zmap, zb, 0, kx, 0, r * nz + n, blockIdx.y);
+                    bulk_commit();
+                    bulk_wait_read_all();  // the slot has been read: it may be refilled
+                }
+                __syncwarp();
+                mbar_arrive(&zempty[sz]);
             } else {
+                mbar_arrive(&zempty[sz]);  // this lane is done with the slot (transposes included)
                 C* dst = Z + ((size_t)(r * a.kx_count + kx) * nz + n) * a.ny_pad;
 #pragma unroll
                 for (int j = 0; j < 32; ++j) {
@@ -218,6 +222,7 @@ __global__ void __maxnreg__(AwShape::REGS)
                 }
             }
         }
+        if (a.z_tiled && lane == 0) bulk_wait_all();  // every tensor store has landed
         cta_sync_or(failed || *abort);
     }
 }

@@ -82,8 +82,11 @@ cudaError_t adjoint_wf_launch(const ColumnArgs& a, const AwSmem& L, const void* 
     constexpr auto k = adjoint_column_wf_kernel<NC>;
     cudaError_t e = ensure_smem_limit<k>();
     if (e != cudaSuccess) return e;
+    CUtensorMap zmap{};
+    if (a.z_tiled && (e = make_ztile_map(&zmap, Z, a.nz, a.ny_pad, a.kx_count, b.count, b.out)) != cudaSuccess)
+        return e;
     k<<<dim3(2 * a.kx_count, b.count), AwShape::NT, L.total, s>>>(a, L, (const float2*)Xr, spec, (float2*)Z,
-                                                                   (const float2*)tw, err, b.in, b.out);
+                                                                   (const float2*)tw, err, b.in, b.out, zmap);
     return cudaGetLastError();
 }
 
