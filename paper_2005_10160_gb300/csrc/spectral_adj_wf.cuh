@@ -40,7 +40,11 @@ struct AwSmem {
     uint32_t slot_off, tw_off, t2_off, bar_off, flag_off, total;
 };
 
-template <int NC>
+// IM, OV: the plan's imaginary-spectrum and odd-in-y component masks when
+// known at compile time (the all-six-components request), else kRuntimeMask.
+constexpr unsigned kRuntimeMask = ~0u;
+
+template <int NC, unsigned IM = kRuntimeMask, unsigned OV = kRuntimeMask>
 __global__ void __maxnreg__(AwShape::REGS)
     adjoint_column_wf_kernel(ColumnArgs a, AwSmem L, const float2* __restrict__ Xr, const float* __restrict__ spec,
                              float2* __restrict__ Z, const float2* __restrict__ tw, int* __restrict__ err,
@@ -115,7 +119,8 @@ __global__ void __maxnreg__(AwShape::REGS)
             rc[c][0] = ring[c * FS + k1];
             rc[c][1] = ring[c * FS + k2];
         }
-        const unsigned imag = a.imag_mask, flip = nyq ? 0u : a.oddv_mask;
+        const unsigned imag = IM == kRuntimeMask ? a.imag_mask : IM;
+        const unsigned oddv = OV == kRuntimeMask ? a.oddv_mask : OV;
         cta_sync();  // every combine thread has its bins: the slots become the ring
         const float* Sq = Sk + q;
         float sv[NC], se[NC];
@@ -144,7 +149,7 @@ __global__ void __maxnreg__(AwShape::REGS)
 #pragma unroll
             for (int c = 0; c < NC; ++c) {
                 const float s1 = sv[c];
-                const float s2 = nyq ? se[c] : (((flip >> c) & 1u) ? -s1 : s1);
+                const float s2 = nyq ? se[c] : (((oddv >> c) & 1u) ? -s1 : s1);
                 const C v1 = rc[c][0], v2 = rc[c][1];
                 // conj(S) v with S = s (real spectrum) or i s (imaginary spectrum)
                 if ((imag >> c) & 1u) {

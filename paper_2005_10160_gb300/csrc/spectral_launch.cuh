@@ -76,10 +76,10 @@ cudaError_t forward_impl(const ColumnArgs& a, const void* X, const R* spec, void
         }                                                                                               \
     }
 
-template <int NC>
+template <int NC, unsigned IM = kRuntimeMask, unsigned OV = kRuntimeMask>
 cudaError_t adjoint_wf_launch(const ColumnArgs& a, const AwSmem& L, const void* Xr, const float* spec, void* Z,
                               const void* tw, int* err, cudaStream_t s, Batch b) {
-    constexpr auto k = adjoint_column_wf_kernel<NC>;
+    constexpr auto k = adjoint_column_wf_kernel<NC, IM, OV>;
     cudaError_t e = ensure_smem_limit<k>();
     if (e != cudaSuccess) return e;
     CUtensorMap zmap{};
@@ -104,7 +104,11 @@ cudaError_t adjoint_impl(const ColumnArgs& a, const void* Xr, const R* spec, voi
                 case 3: return adjoint_wf_launch<3>(a, L, Xr, spec, Z, tw, err, s, b);
                 case 4: return adjoint_wf_launch<4>(a, L, Xr, spec, Z, tw, err, s, b);
                 case 5: return adjoint_wf_launch<5>(a, L, Xr, spec, Z, tw, err, s, b);
-                case 6: return adjoint_wf_launch<6>(a, L, Xr, spec, Z, tw, err, s, b);
+                case 6:
+                    // all six components: masks known at compile time
+                    if (a.imag_mask == 0x28u && a.oddv_mask == 0x24u)
+                        return adjoint_wf_launch<6, 0x28u, 0x24u>(a, L, Xr, spec, Z, tw, err, s, b);
+                    return adjoint_wf_launch<6>(a, L, Xr, spec, Z, tw, err, s, b);
                 case 7: return adjoint_wf_launch<7>(a, L, Xr, spec, Z, tw, err, s, b);
                 default: break;
             }
