@@ -105,11 +105,16 @@ cudaError_t adjoint_impl(const ColumnArgs& a, const void* Xr, const R* spec, voi
                 case 4: return adjoint_wf_launch<4>(a, L, Xr, spec, Z, tw, err, s, b);
                 case 5: return adjoint_wf_launch<5>(a, L, Xr, spec, Z, tw, err, s, b);
                 case 6:
-                    // all six components: masks known at compile time
+                    // all six components (gz, gxx, gxy, gxz, gyy, gyz): gxz and gyz have
+                    // imaginary spectra, gxy and gyz are odd in y; masks known at compile time
                     if (a.imag_mask == 0x28u && a.oddv_mask == 0x24u)
                         return adjoint_wf_launch<6, 0x28u, 0x24u>(a, L, Xr, spec, Z, tw, err, s, b);
                     return adjoint_wf_launch<6>(a, L, Xr, spec, Z, tw, err, s, b);
-                case 7: return adjoint_wf_launch<7>(a, L, Xr, spec, Z, tw, err, s, b);
+                case 7:
+                    // all seven components (gzz adds an even, real spectrum): same masks
+                    if (a.imag_mask == 0x28u && a.oddv_mask == 0x24u)
+                        return adjoint_wf_launch<7, 0x28u, 0x24u>(a, L, Xr, spec, Z, tw, err, s, b);
+                    return adjoint_wf_launch<7>(a, L, Xr, spec, Z, tw, err, s, b);
                 default: break;
             }
         }
