@@ -60,7 +60,7 @@ def parse():
     ap.add_argument("--workload", choices=tuple(WORKLOADS), default="grf1024")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-fp64", action="store_true", help="skip the FP64-spectral comparison leg")
-    ap.add_argument("--serve-requests", type=int, default=1000,
+    ap.add_argument("--serve-requests", type=int, default=10000,
                     help="requests in the serving leg (Poisson arrivals, 0 to skip)")
     ap.add_argument("--serve-rate", type=float, default=200.0, help="mean arrival rate of the serving leg (1/s)")
     return ap.parse_args()
@@ -270,6 +270,7 @@ def serving_leg(n_requests: int, rate: float):
         t_next = t0
         pairs = 0.0
         reqs = []
+        swept = 0
         for _ in range(n_requests):
             t_next += float(rng.exponential(1.0 / rate))
             i = int(rng.integers(4))
@@ -280,6 +281,10 @@ def serving_leg(n_requests: int, rate: float):
                 time.sleep(delay)  # sleeping releases the GIL to the server thread
             reqs.append(srv.submit(kind, m, pool[(i, kind)][int(rng.integers(4))]))
             pairs += pairs_per_forward(m.tuple())
+            # results are not needed here: free them as requests finish (only the timings are kept)
+            while swept < len(reqs) and reqs[swept].done.is_set():
+                reqs[swept].result = None
+                swept += 1
         srv.drain()
         for r in reqs:
             r.wait(60)
@@ -512,6 +517,27 @@ def run_ours(args):
         plan64.close()
         del rho64, out64
 
+    # the full inversion loop (damped CGLS with depth weights) on the 512^2 x 64
+    # three-box model, gz + gzz data with 1% noise: one forward and one adjoint
+    # per iteration through the C ABI
+    inversion = None
+    if rank == 0 and args.workload == "grf1024":
+        from paper_2005_10160_gb300.inversion import cg_step, cgls, noisy_data
+
+        imesh, irho, _ = workloads.boxes512()
+        icomps = capi.GRAV_GZ | capi.GRAV_GZZ
+        with Plan(imesh, icomps) as ip:
+            clean = ip.forward(torch.as_tensor(irho, dtype=torch.float32, device=dev))
+            d_i, w_i = noisy_data(clean.cpu(), 0.01, seed=workloads.SEED_BASE + 4)
+            d_i, w_i = d_i.to(dev), w_i.to(dev)
+            lam_i = cg_step(ip, d_i, w_i).lam
+            cgls(ip, d_i, w_i, lam_i, iters=2)  # warm-up
+            res = cgls(ip, d_i, w_i, lam_i, iters=10)
+        inversion = {"workload": "512x512x64 cubes of 20 m, three boxes, gz + gzz data with 1% noise, "
+                                 "depth weights beta = 2, damped CGLS",
+                     "iterations": res.iterations, "ms_per_iteration": res.ms_per_iteration,
+                     "lam": res.lam, "objective_first": res.objectives[0], "objective_last": res.objectives[-1]}
+
     serving = None
     if rank == 0 and args.serve_requests > 0:
         plan.close()
@@ -537,7 +563,7 @@ def run_ours(args):
                        "parallelism": f"replica x{world}", "plan_create_s": plan_s,
                        "forward_algorithmic_bytes": fwd_alg},
             "roofline": roofline, "clocks": clocks, "e2e": e2e, "gpu_launches": 3 * args.steps,
-            "cpu_baseline": cpu, "fp64_path": fp64, "adjoint": adjoint, "serving": serving,
+            "cpu_baseline": cpu, "fp64_path": fp64, "adjoint": adjoint, "inversion": inversion, "serving": serving,
         }
         print(json.dumps(line), flush=True)
     plan.close()
