@@ -11,7 +11,7 @@ The arithmetic lives in ``prism_oracle.c``; this module only compiles it with
 gcc and marshals numpy arrays.
 
 Component bits (ascending bit order is the row order of every output):
-1 gz, 2 gxx, 4 gxy, 8 gxz, 16 gyy, 32 gyz, 64 gzz.
+1 gz, 2 gxx, 4 gxy, 8 gxz, 16 gyy, 32 gyz, 64 gzz, 128 gx, 256 gy.
 """
 from __future__ import annotations
 
@@ -30,7 +30,7 @@ _LIB_PATH = os.path.join(_HERE, "_prism_oracle.so")
 _lock = threading.Lock()
 _lib = None
 
-COMPONENTS = ("gz", "gxx", "gxy", "gxz", "gyy", "gyz", "gzz")
+COMPONENTS = ("gz", "gxx", "gxy", "gxz", "gyy", "gyz", "gzz", "gx", "gy")
 UPSILON = 6.672e-11
 
 
@@ -82,7 +82,7 @@ def _load():
 
 def comp_list(comps: int) -> list[int]:
     """Component indices selected by a bit mask, in ascending bit order."""
-    return [c for c in range(7) if comps & (1 << c)]
+    return [c for c in range(len(COMPONENTS)) if comps & (1 << c)]
 
 
 def default_threads() -> int:
@@ -90,13 +90,13 @@ def default_threads() -> int:
 
 
 def prism(station, box) -> np.ndarray:
-    """Kernel per unit density of one prism at one station, all 7 components.
+    """Kernel per unit density of one prism at one station, all 9 components.
 
     station = (x, y, z); box = (xi1, xi2, eta1, eta2, zeta1, zeta2); z positive
     down.  Returns [gz, gxx, gxy, gxz, gyy, gyz, gzz] in SI units (Eq. 2 and
     the standard gradient forms)."""
     lib = _load()
-    out = np.zeros(7, dtype=np.float64)
+    out = np.zeros(len(COMPONENTS), dtype=np.float64)
     lib.orc_prism(*[float(v) for v in station], *[float(v) for v in box],
                   out.ctypes.data_as(ctypes.c_void_p))
     return out

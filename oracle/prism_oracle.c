@@ -27,6 +27,13 @@
  *   gzz: F =  atan(x y / (z r))      gxy: F = -asinh(z / sqrt(x^2 + y^2))
  *   gxz: F = -asinh(y / sqrt(x^2 + z^2))
  *   gyz: F = -asinh(x / sqrt(y^2 + z^2))
+ *   The horizontal first derivatives gx, gy (the x and y counterparts of gz,
+ *   positive towards +x and +y) are the same eight-corner form with the axes
+ *   permuted cyclically (z -> x, resp. z -> y, as the distinguished axis):
+ *   gx:  F = -[y asinh(z/sqrt(x^2+y^2)) + z asinh(y/sqrt(x^2+z^2))
+ *              - x atan(y z / (x r))]
+ *   gy:  F = -[z asinh(x/sqrt(y^2+z^2)) + x asinh(z/sqrt(x^2+y^2))
+ *              - y atan(x z / (y r))]
  *
  * Geometry (the mesh of Fig. 1 and the index order of Sec. 2.2,
  * j = l + nx*m + nx*ny*n):
@@ -36,7 +43,7 @@
  * Units: density kg/m^3, gz in m/s^2, gradients in 1/s^2.
  *
  * Component bits (ascending bit order is the output row order):
- *   1 gz, 2 gxx, 4 gxy, 8 gxz, 16 gyy, 32 gyz, 64 gzz.
+ *   1 gz, 2 gxx, 4 gxy, 8 gxz, 16 gyy, 32 gyz, 64 gzz, 128 gx, 256 gy.
  */
 #include <math.h>
 #include <pthread.h>
@@ -44,11 +51,11 @@
 #include <string.h>
 
 #define ORC_UPSILON 6.672e-11
-#define ORC_NCOMP_MAX 7
+#define ORC_NCOMP_MAX 9
 
-/* Eight-corner sums for one prism seen from one station, all seven
- * components, per unit density and including upsilon.  out[0..6] =
- * gz, gxx, gxy, gxz, gyy, gyz, gzz. */
+/* Eight-corner sums for one prism seen from one station, all nine
+ * components, per unit density and including upsilon.  out[0..8] =
+ * gz, gxx, gxy, gxz, gyy, gyz, gzz, gx, gy. */
 void orc_prism(double x, double y, double z,
                double xi1, double xi2, double eta1, double eta2,
                double zeta1, double zeta2, double out[ORC_NCOMP_MAX])
@@ -56,7 +63,7 @@ void orc_prism(double x, double y, double z,
     const double xs[2] = {x - xi1, x - xi2};
     const double ys[2] = {y - eta1, y - eta2};
     const double zs[2] = {z - zeta1, z - zeta2};
-    double acc[ORC_NCOMP_MAX] = {0, 0, 0, 0, 0, 0, 0};
+    double acc[ORC_NCOMP_MAX] = {0};
     for (int i = 0; i < 2; ++i) {
         for (int j = 0; j < 2; ++j) {
             for (int k = 0; k < 2; ++k) {
@@ -80,6 +87,8 @@ void orc_prism(double x, double y, double z,
                 acc[4] += mu * t_y;
                 acc[5] += mu * -a_x;
                 acc[6] += mu * t_z;
+                acc[7] += mu * -(yj * a_z + zk * a_y - xi * t_x);
+                acc[8] += mu * -(zk * a_x + xi * a_z - yj * t_y);
             }
         }
     }
@@ -131,7 +140,7 @@ static void* orc_forward_worker(void* arg)
     for (int s = jb->tid; s < jb->n_idx; s += jb->nthreads) {
         const int st = jb->idx[s];
         const int p = st % g->nx, q = st / g->nx;
-        double acc[ORC_NCOMP_MAX] = {0, 0, 0, 0, 0, 0, 0};
+        double acc[ORC_NCOMP_MAX] = {0};
         for (int n = 0; n < g->nz; ++n)
             for (int m = 0; m < g->ny; ++m)
                 for (int l = 0; l < g->nx; ++l) {
@@ -198,7 +207,7 @@ static int orc_check(int nx, int ny, int nz, double dx, double dy, double dz,
 {
     if (nx <= 0 || ny <= 0 || nz <= 0) return -1;
     if (!(dx > 0) || !(dy > 0) || !(dz > 0) || !(h > 0)) return -1;
-    if (comps == 0 || (comps & ~0x7Fu)) return -1;
+    if (comps == 0 || (comps & ~0x1FFu)) return -1;
     return 0;
 }
 

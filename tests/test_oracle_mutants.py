@@ -30,6 +30,8 @@ MUTANTS = {
     "layer_index": ("n * g->dz, (n + 1) * g->dz", "(n + 1) * g->dz, (n + 2) * g->dz"),
     "rho_index_swapped": ("rho[((size_t)n * g->ny + m) * g->nx + l]", "rho[((size_t)n * g->nx + l) * g->ny + m]"),
     "atan_gxx_gyy_swapped": ("acc[1] += mu * t_x;", "acc[1] += mu * t_y;"),
+    "sign_gx_atan": ("- xi * t_x);", "+ xi * t_x);"),
+    "gy_asinh_swapped": ("zk * a_x + xi * a_z", "zk * a_z + xi * a_x"),
 }
 
 
@@ -53,7 +55,7 @@ def _pins_pass(lib):
     """True when the library passes the quadrature and superposition pins."""
     for station, box in [((13.0, -4.0, -7.0), (0.0, 10.0, 0.0, 20.0, 0.0, 15.0)),
                          ((2.0, 30.0, -3.0), (0.0, 10.0, 0.0, 20.0, 0.0, 15.0))]:
-        out = np.zeros(7)
+        out = np.zeros(9)
         lib.orc_prism(*station, *box, out.ctypes.data_as(ctypes.c_void_p))
         ref = prism_quadrature(station, box, nsub=4, order=16)
         if np.abs(out - ref).max() > 1e-9 * np.abs(ref).max():
@@ -71,7 +73,7 @@ def _pins_pass(lib):
         station = ((p_ + 0.5) * dx, (q_ + 0.5) * dy, -h)
         box = (2 * dx, 5 * dx, 1 * dy, 4 * dy, 1 * dz, 3 * dz)
         ref = prism_quadrature(station, box, nsub=2, order=12) if s % 7 == 0 else None
-        if ref is not None and np.abs(got[:, s] - ref).max() > 1e-7 * np.abs(ref).max():
+        if ref is not None and np.abs(got[:, s] - ref[:7]).max() > 1e-7 * np.abs(ref[:7]).max():
             return False
     return True
 

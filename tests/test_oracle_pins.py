@@ -27,8 +27,9 @@ ALL7 = 0x7F
     ],
 )
 def test_closed_forms_match_quadrature(orc, station, box):
-    """All seven closed forms (Eq. 2 and the gradient forms) equal brute-force
-    Gauss-Legendre quadrature of the volume integrals."""
+    """All nine closed forms (Eq. 2, the gradient forms and the horizontal
+    first derivatives) equal brute-force Gauss-Legendre quadrature of the
+    volume integrals."""
     ref = prism_quadrature(station, box, nsub=8, order=16)
     got = orc.prism(station, box)
     scale = np.abs(ref).max()
@@ -115,6 +116,34 @@ def test_gz_finite_differences(orc, station):
     assert abs(d_dir(0) - g0[3]) <= 1e-7 * scale
     assert abs(d_dir(1) - g0[5]) <= 1e-7 * scale
     assert abs(d_dir(2) - g0[6]) <= 1e-7 * scale
+
+
+@pytest.mark.parametrize("station", [(3.0, 4.0, -2.0), (-12.0, 7.0, -5.0), (25.0, 25.0, -1.5)])
+def test_gx_gy_finite_differences(orc, station):
+    """The horizontal first derivatives against the gradient tensor: d(gx)/dx
+    = gxx, d(gx)/dy = gxy, d(gx)/dz = gxz, d(gy)/dy = gyy, d(gy)/dz = gyz
+    (fourth-order central differences of the gx, gy closed forms)."""
+    box = (0.0, 10.0, 0.0, 20.0, 0.0, 15.0)
+    e = 1e-2
+    st = np.asarray(station, float)
+    g0 = orc.prism(st, box)
+
+    def d_dir(comp, axis):
+        def g(off):
+            s = st.copy()
+            s[axis] += off
+            return orc.prism(s, box)[comp]
+
+        return (-g(2 * e) + 8 * g(e) - 8 * g(-e) + g(-2 * e)) / (12 * e)
+
+    scale = np.abs(g0[1:7]).max()
+    GX, GY = 7, 8
+    assert abs(d_dir(GX, 0) - g0[1]) <= 1e-7 * scale
+    assert abs(d_dir(GX, 1) - g0[2]) <= 1e-7 * scale
+    assert abs(d_dir(GX, 2) - g0[3]) <= 1e-7 * scale
+    assert abs(d_dir(GY, 0) - g0[2]) <= 1e-7 * scale
+    assert abs(d_dir(GY, 1) - g0[4]) <= 1e-7 * scale
+    assert abs(d_dir(GY, 2) - g0[5]) <= 1e-7 * scale
 
 
 def _gmesh():
