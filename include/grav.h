@@ -50,7 +50,10 @@ extern "C" {
 typedef struct grav_plan grav_plan;
 
 /* Component mask bits (Eq. 1): the five independent gradient components,
- * gz (Eq. 2) and the derived gzz = -(gxx + gyy). */
+ * gz (Eq. 2) and the derived gzz = -(gxx + gyy); and the horizontal first
+ * derivatives gx, gy (also block Toeplitz, shown in Fig. 6), positive towards
+ * +x and +y.  One plan holds at most 8 components (GRAV_EINVAL above that:
+ * split the request over two plans). */
 enum {
     GRAV_GZ = 1,
     GRAV_GXX = 2,
@@ -59,6 +62,8 @@ enum {
     GRAV_GYY = 16,
     GRAV_GYZ = 32,
     GRAV_GZZ = 64,
+    GRAV_GX = 128,
+    GRAV_GY = 256,
     GRAV_ALL6 = 63,
     /* Precision flag: FP64 input, spectra, FFTs and output.  Without it the
      * spectra are stored as FP32 and the per-call arithmetic is FP32 with a
@@ -87,7 +92,8 @@ enum {
  *               nz >= 1
  *   dx, dy, dz  cell size in metres, > 0
  *   h           station height above the mesh top in metres, > 0
- *   components  OR of GRAV_GZ ... GRAV_GZZ, optionally | GRAV_FP64_SPECTRAL
+ *   components  OR of GRAV_GZ ... GRAV_GY (at most 8 of them), optionally
+ *               | GRAV_FP64_SPECTRAL
  * Returns NULL on error (GRAV_EINVAL or GRAV_ENOMEM class, see
  * grav_last_error). */
 grav_plan* grav_plan_create(int nx, int ny, int nz, double dx, double dy, double dz,

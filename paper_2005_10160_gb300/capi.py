@@ -13,7 +13,10 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(HERE, "libgravfft.so")
 
 GRAV_GZ, GRAV_GXX, GRAV_GXY, GRAV_GXZ, GRAV_GYY, GRAV_GYZ, GRAV_GZZ = 1, 2, 4, 8, 16, 32, 64
+GRAV_GX, GRAV_GY = 128, 256
 GRAV_ALL6 = 63
+GRAV_COMP_BITS = 0x1FF  # every component bit
+GRAV_MAX_PLAN_COMPONENTS = 8
 GRAV_FP64_SPECTRAL = 1 << 16
 GRAV_OK, GRAV_EINVAL, GRAV_ENOMEM, GRAV_ECUDA, GRAV_ETIMEOUT = 0, -1, -2, -3, -4
 GRAV_MAX_NX, GRAV_MAX_NY = 2048, 1024
@@ -159,7 +162,7 @@ def grav_kernel_values(nx, ny, nz, dx, dy, dz, h, components, K_ptr, stream=0) -
 
 
 def comp_list(components: int) -> list[int]:
-    return [c for c in range(7) if components & (1 << c)]
+    return [c for c in range(9) if components & (1 << c)]
 
 
 def grav_plan_set_timing(plan, enable: bool) -> int:

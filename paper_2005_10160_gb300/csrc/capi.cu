@@ -84,8 +84,13 @@ int check_geometry(int nx, int ny, int nz, double dx, double dy, double dz, doub
         set_error("station height h must be finite and > 0 (got %g)", h);
         return GRAV_EINVAL;
     }
-    if ((components & 0x7Fu) == 0 || (components & ~(0x7Fu | (unsigned)GRAV_FP64_SPECTRAL))) {
+    if ((components & kCompBits) == 0 || (components & ~(kCompBits | (unsigned)GRAV_FP64_SPECTRAL))) {
         set_error("component mask 0x%x selects no component or has unknown bits", components);
+        return GRAV_EINVAL;
+    }
+    if (__builtin_popcount(components & kCompBits) > kMaxPlanComp) {
+        set_error("component mask 0x%x selects more than %d components; split it into two plans", components,
+                  kMaxPlanComp);
         return GRAV_EINVAL;
     }
     if ((size_t)nz * (size_t)ny * (size_t)nx > (size_t)1 << 31) {
@@ -367,7 +372,7 @@ grav_plan* grav_plan_create(int nx, int ny, int nz, double dx, double dy, double
     }
     p->nx = nx; p->ny = ny; p->nz = nz;
     p->dx = dx; p->dy = dy; p->dz = dz; p->h = h;
-    p->comps = components & 0x7Fu;
+    p->comps = components & kCompBits;
     p->fp64 = (components & GRAV_FP64_SPECTRAL) ? 1 : 0;
     for (int c = 0; c < kMaxComp; ++c) {
         if (p->comps & (1u << c)) {
@@ -485,7 +490,7 @@ int grav_kernel_values(int nx, int ny, int nz, double dx, double dy, double dz, 
         return GRAV_EINVAL;
     }
     Geometry g{nx, ny, nz, dx, dy, dz, h};
-    cudaError_t e = launch_kernel_gen(g, components & 0x7Fu, 0, nz, 1, 0, 0, K_dev, (cudaStream_t)stream);
+    cudaError_t e = launch_kernel_gen(g, components & kCompBits, 0, nz, 1, 0, 0, K_dev, (cudaStream_t)stream);
     if (e != cudaSuccess) return cuda_fail(e, "kernel generation launch");
     return GRAV_OK;
 }

@@ -12,14 +12,16 @@
 
 namespace grav {
 
-constexpr int kMaxComp = 7;
+constexpr int kMaxComp = 9;        // component bits 0 .. 8 (gz ... gzz, gx, gy)
+constexpr int kMaxPlanComp = 8;    // components one plan may hold
+constexpr unsigned kCompBits = (1u << kMaxComp) - 1;
 constexpr double kUpsilon = 6.672e-11;  // gravitational constant of Sec. 2.1
 
 // Parity of each component's kernel under x -> -x and y -> -y (the
-// symmetries of Sec. 2.2): gz, gxx, gxy, gxz, gyy, gyz, gzz.
+// symmetries of Sec. 2.2): gz, gxx, gxy, gxz, gyy, gyz, gzz, gx, gy.
 // Bit c set = component c is odd in that direction.
-constexpr unsigned kOddUMask = 0x0Cu;  // gxy, gxz
-constexpr unsigned kOddVMask = 0x24u;  // gxy, gyz
+constexpr unsigned kOddUMask = 0x8Cu;   // gxy, gxz, gx
+constexpr unsigned kOddVMask = 0x124u;  // gxy, gyz, gy
 __host__ __device__ constexpr bool odd_u(int c) { return (kOddUMask >> c) & 1u; }
 __host__ __device__ constexpr bool odd_v(int c) { return (kOddVMask >> c) & 1u; }
 

@@ -13,6 +13,10 @@
 //     gxx: atan(yz/(xr))   gyy: atan(xz/(yr))   gzz: atan(xy/(zr))
 //     gxy: -asinh(z/sqrt(x^2+y^2))   gxz: -asinh(y/sqrt(x^2+z^2))
 //     gyz: -asinh(x/sqrt(y^2+z^2))
+// and for the horizontal first derivatives the gz form with x (resp. y) as
+// the distinguished axis:
+//     gx: -[y asinh(z/sqrt(x^2+y^2)) + z asinh(y/sqrt(x^2+z^2)) - x atan(yz/(xr))]
+//     gy: -[z asinh(x/sqrt(y^2+z^2)) + x asinh(z/sqrt(x^2+y^2)) - y atan(xz/(yr))]
 // FP64 throughout: the eight corner terms cancel to a few parts in 1e7 at
 // the far offsets of a 1024-cell mesh, so FP32 generation is unusable.
 //
@@ -27,16 +31,19 @@ namespace grav {
 
 namespace {
 
-__device__ __forceinline__ void corner_terms(double x, double y, double z, unsigned comps, double F[kMaxComp]) {
+// NC: components kept per corner, 7 (gz ... gzz) or 9 (with gx, gy); plans
+// without gx, gy use 7 so that the kernel keeps fewer registers.
+template <int NC>
+__device__ __forceinline__ void corner_terms(double x, double y, double z, unsigned comps, double (&F)[NC]) {
     const double x2 = x * x, y2 = y * y, z2 = z * z;
     const double r = sqrt(x2 + y2 + z2);
     double ay = 0.0, ax = 0.0, az = 0.0, tz = 0.0, tx = 0.0, ty = 0.0;
-    if (comps & (GRAV_GZ | GRAV_GXZ)) ay = asinh(y / sqrt(x2 + z2));
-    if (comps & (GRAV_GZ | GRAV_GYZ)) ax = asinh(x / sqrt(y2 + z2));
-    if (comps & GRAV_GXY) az = asinh(z / sqrt(x2 + y2));
+    if (comps & (GRAV_GZ | GRAV_GXZ | GRAV_GX)) ay = asinh(y / sqrt(x2 + z2));
+    if (comps & (GRAV_GZ | GRAV_GYZ | GRAV_GY)) ax = asinh(x / sqrt(y2 + z2));
+    if (comps & (GRAV_GXY | GRAV_GX | GRAV_GY)) az = asinh(z / sqrt(x2 + y2));
     if (comps & (GRAV_GZ | GRAV_GZZ)) tz = atan(x * y / (z * r));
-    if (comps & GRAV_GXX) tx = atan(y * z / (x * r));
-    if (comps & GRAV_GYY) ty = atan(x * z / (y * r));
+    if (comps & (GRAV_GXX | GRAV_GX)) tx = atan(y * z / (x * r));
+    if (comps & (GRAV_GYY | GRAV_GY)) ty = atan(x * z / (y * r));
     F[0] = -(x * ay + y * ax - z * tz);
     F[1] = tx;
     F[2] = -az;
@@ -44,8 +51,13 @@ __device__ __forceinline__ void corner_terms(double x, double y, double z, unsig
     F[4] = ty;
     F[5] = -ax;
     F[6] = tz;
+    if constexpr (NC > 7) {
+        F[7] = -(y * az + z * ay - x * tx);  // gx: the gz form with x as the distinguished axis
+        F[8] = -(z * ax + x * az - y * ty);  // gy: the same with y
+    }
 }
 
+template <int NC>
 __global__ void kernel_gen(Geometry g, unsigned comps, int n0, int n1, int mode, int px, int py, double* __restrict__ out) {
     const int u = blockIdx.x * blockDim.x + threadIdx.x;
     const int v = blockIdx.y;
@@ -53,7 +65,7 @@ __global__ void kernel_gen(Geometry g, unsigned comps, int n0, int n1, int mode,
     const double xs[2] = {(0.5 - u) * g.dx, -(0.5 + u) * g.dx};
     const double ys[2] = {(0.5 - v) * g.dy, -(0.5 + v) * g.dy};
 
-    double top[4][kMaxComp];
+    double top[4][NC];
     {
         const double z = -g.h - n0 * g.dz;
 #pragma unroll
@@ -62,12 +74,12 @@ __global__ void kernel_gen(Geometry g, unsigned comps, int n0, int n1, int mode,
     const int nzc = n1 - n0;
     const int wx = 2 * g.nx - 1, wy = 2 * g.ny - 1;
     for (int n = n0; n < n1; ++n) {
-        double bot[4][kMaxComp];
+        double bot[4][NC];
         const double z = -g.h - (n + 1) * g.dz;
 #pragma unroll
         for (int ij = 0; ij < 4; ++ij) corner_terms(xs[ij >> 1], ys[ij & 1], z, comps, bot[ij]);
 #pragma unroll
-        for (int c = 0; c < kMaxComp; ++c) {
+        for (int c = 0; c < NC; ++c) {
             if (!(comps & (1u << c))) continue;
             const int s = __popc(comps & ((1u << c) - 1u));  // output slot of component c
             // mu_ijk: +1 for the bottom z-level when i + j is even
@@ -97,7 +109,7 @@ __global__ void kernel_gen(Geometry g, unsigned comps, int n0, int n1, int mode,
 #pragma unroll
         for (int ij = 0; ij < 4; ++ij)
 #pragma unroll
-            for (int c = 0; c < kMaxComp; ++c) top[ij][c] = bot[ij][c];
+            for (int c = 0; c < NC; ++c) top[ij][c] = bot[ij][c];
     }
 }
 
@@ -107,7 +119,11 @@ cudaError_t launch_kernel_gen(const Geometry& g, unsigned comps, int n0, int n1,
                               double* out, cudaStream_t s) {
     const int bx = 64;
     dim3 grid((g.nx + bx - 1) / bx, g.ny);
-    kernel_gen<<<grid, bx, 0, s>>>(g, comps & 0x7Fu, n0, n1, mode, px, py, out);
+    comps &= kCompBits;
+    if (comps & (GRAV_GX | GRAV_GY))
+        kernel_gen<9><<<grid, bx, 0, s>>>(g, comps, n0, n1, mode, px, py, out);
+    else
+        kernel_gen<7><<<grid, bx, 0, s>>>(g, comps, n0, n1, mode, px, py, out);
     return cudaGetLastError();
 }
 

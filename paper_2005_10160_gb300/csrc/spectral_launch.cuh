@@ -54,7 +54,8 @@ cudaError_t forward_impl(const ColumnArgs& a, const void* X, const R* spec, void
         case 4: return forward_impl<R, L, 4>(a, in, spec, out, tw, err, s, b);   \
         case 5: return forward_impl<R, L, 5>(a, in, spec, out, tw, err, s, b);   \
         case 6: return forward_impl<R, L, 6>(a, in, spec, out, tw, err, s, b);   \
-        default: return forward_impl<R, L, 7>(a, in, spec, out, tw, err, s, b);  \
+        case 7: return forward_impl<R, L, 7>(a, in, spec, out, tw, err, s, b);   \
+        default: return forward_impl<R, L, 8>(a, in, spec, out, tw, err, s, b);  \
     }
 
 #define GRAV_FORWARD_LAUNCHER(R)                                                                        \
@@ -115,6 +116,7 @@ cudaError_t adjoint_impl(const ColumnArgs& a, const void* Xr, const R* spec, voi
                     if (a.imag_mask == 0x28u && a.oddv_mask == 0x24u)
                         return adjoint_wf_launch<7, 0x28u, 0x24u>(a, L, Xr, spec, Z, tw, err, s, b);
                     return adjoint_wf_launch<7>(a, L, Xr, spec, Z, tw, err, s, b);
+                case 8: return adjoint_wf_launch<8>(a, L, Xr, spec, Z, tw, err, s, b);
                 default: break;
             }
         }

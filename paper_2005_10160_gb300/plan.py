@@ -15,7 +15,7 @@ class Plan:
     device.
 
     mesh: (nx, ny, nz, dx, dy, dz, h) or an object with those attributes.
-    components: OR of capi.GRAV_GZ ... GRAV_GZZ.
+    components: OR of capi.GRAV_GZ ... GRAV_GY (at most 8).
     fp64: FP64 spectra and arithmetic (float64 tensors) instead of FP32.
     """
 
@@ -24,7 +24,7 @@ class Plan:
             mesh = mesh.tuple()
         nx, ny, nz, dx, dy, dz, h = mesh
         self.mesh = (int(nx), int(ny), int(nz), float(dx), float(dy), float(dz), float(h))
-        self.components = int(components) & 0x7F
+        self.components = int(components) & capi.GRAV_COMP_BITS
         self.fp64 = bool(fp64)
         if not torch.cuda.is_available():
             raise RuntimeError("libgravfft needs a CUDA device")

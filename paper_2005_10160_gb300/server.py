@@ -186,7 +186,7 @@ class Server:
         py = 4
         while py < 2 * ny - 1:
             py *= 2
-        nc = bin(comps & 0x7F).count("1")
+        nc = bin(comps & capi.GRAV_COMP_BITS).count("1")
         real = 8 if fp64 else 4
         kx = px // 2 + 1
         ny_pad = (ny + 3) // 4 * 4

@@ -35,6 +35,8 @@ def test_library_exports_every_declared_symbol(gravlib):
         ((4, 4, 4, 1.0, -1.0, 1.0, 1.0, 1), "cell sizes"),
         ((4, 4, 4, 1.0, 1.0, 1.0, 1.0, 0), "component"),
         ((4, 4, 4, 1.0, 1.0, 1.0, 1.0, 1 << 20), "component"),
+        ((4, 4, 4, 1.0, 1.0, 1.0, 1.0, 1 << 9), "component"),
+        ((4, 4, 4, 1.0, 1.0, 1.0, 1.0, 0x1FF), "more than 8 components"),
         ((capi.GRAV_MAX_NX + 1, 4, 4, 1.0, 1.0, 1.0, 1.0, 1), "mesh size"),
         ((4, capi.GRAV_MAX_NY + 1, 4, 1.0, 1.0, 1.0, 1.0, 1), "mesh size"),
         ((4, 4, 4, float("nan"), 1.0, 1.0, 1.0, 1), "cell sizes"),

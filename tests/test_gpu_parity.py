@@ -5,8 +5,8 @@ Bars (per component, relative L2 over the compared stations or cells):
   FP32 spectral path vs the oracle / FP64     <= 2e-5
 Components that vanish by symmetry (e.g. gxz on a one-column mesh) are
 compared against a floor of 1e-3 times the largest component norm of the
-same kind (gz alone, or the gradients), so rounding noise in the oracle does
-not count as a relative error.
+same kind (first derivatives gz, gx, gy, or the gradients), so rounding
+noise in the oracle does not count as a relative error.
 """
 import numpy as np
 import pytest
@@ -18,21 +18,30 @@ from paper_2005_10160_gb300.plan import Plan, kernel_values
 pytestmark = pytest.mark.gpu
 
 ALL7 = 0x7F
+# the six plus the horizontal first derivatives gx, gy (eight components)
+ALL7_GXY_SANS_GZZ = 0x3F | capi.GRAV_GX | capi.GRAV_GY
 TOL64 = 1e-10
 TOL32 = 2e-5
 
 
+FIRST_DERIV = (0, 7, 8)  # gz, gx, gy (m/s^2); the others are second derivatives (1/s^2)
+
+
 def rel_errors(got, ref, comps):
-    """Relative L2 error per component with a symmetry floor."""
+    """Relative L2 error per component with a symmetry floor: 1e-3 of the
+    largest norm among the components of the same kind (first or second
+    derivatives of the potential)."""
     got = np.asarray(got, np.float64).reshape(len(ref), -1)
     ref = np.asarray(ref, np.float64).reshape(len(ref), -1)
     lst = capi.comp_list(comps)
     norms = np.linalg.norm(ref, axis=1)
-    grad = [norms[i] for i, c in enumerate(lst) if c != 0]
-    gmax = max(grad) if grad else 0.0
+    kmax = {}
+    for i, c in enumerate(lst):
+        k = c in FIRST_DERIV
+        kmax[k] = max(kmax.get(k, 0.0), norms[i])
     out = []
     for i, c in enumerate(lst):
-        floor = 1e-3 * (norms[i] if c == 0 else gmax)
+        floor = 1e-3 * kmax[c in FIRST_DERIV]
         den = max(norms[i], floor, 1e-300)
         out.append(np.linalg.norm(got[i] - ref[i]) / den)
     return np.array(out)
@@ -70,15 +79,17 @@ def test_kernel_values_match_oracle(gravlib, orc, mesh):
     """FP64 kernel generation (Eq. 2 and the gradient forms over the offset
     grid of Eq. 10) against the oracle's independent prism evaluation."""
     nx, ny, nz, dx, dy, dz, h = mesh
-    K = kernel_values(mesh, ALL7).cpu().numpy()
-    for n in range(nz):
-        for v in range(-ny + 1, ny):
-            for u in range(-nx + 1, nx):
-                box = ((u - 0.5) * dx, (u + 0.5) * dx, (v - 0.5) * dy, (v + 0.5) * dy, n * dz, (n + 1) * dz)
-                ref = orc.prism((0.0, 0.0, -h), box)
-                got = K[:, n, v + ny - 1, u + nx - 1]
-                scale = np.abs(K[:, n]).reshape(7, -1).max(axis=1)
-                assert np.all(np.abs(got - ref) <= 1e-12 * np.abs(ref) + 1e-13 * scale), (n, u, v, got, ref)
+    for comps in (ALL7, ALL7_GXY_SANS_GZZ):
+        lst = capi.comp_list(comps)
+        K = kernel_values(mesh, comps).cpu().numpy()
+        for n in range(nz):
+            for v in range(-ny + 1, ny):
+                for u in range(-nx + 1, nx):
+                    box = ((u - 0.5) * dx, (u + 0.5) * dx, (v - 0.5) * dy, (v + 0.5) * dy, n * dz, (n + 1) * dz)
+                    ref = orc.prism((0.0, 0.0, -h), box)[lst]
+                    got = K[:, n, v + ny - 1, u + nx - 1]
+                    scale = np.abs(K[:, n]).reshape(len(lst), -1).max(axis=1)
+                    assert np.all(np.abs(got - ref) <= 1e-12 * np.abs(ref) + 1e-13 * scale), (n, u, v, got, ref)
 
 
 @pytest.mark.parametrize("mesh", SMALL_MESHES)
@@ -194,7 +205,7 @@ WIDE_MESHES = [
 
 
 @pytest.mark.parametrize("mesh", WIDE_MESHES)
-@pytest.mark.parametrize("comps", [ALL7, 0x3F, capi.GRAV_GZ, capi.GRAV_GXY | capi.GRAV_GYZ])
+@pytest.mark.parametrize("comps", [ALL7, 0x3F, capi.GRAV_GZ, capi.GRAV_GXY | capi.GRAV_GYZ, ALL7_GXY_SANS_GZZ])
 def test_forward_fp32_wide_columns(gravlib, orc, mesh, comps):
     """FP32 forward on 2048-point columns: against the oracle at sampled
     stations, and against the FP64 spectral path at every station; the FP32
@@ -271,6 +282,25 @@ def test_fp32_adjoint_wide_both(gravlib, mesh):
     lhs = float(np.dot(gx.ravel(), r.ravel()))
     rhs = float(np.dot(x.ravel(), g32.astype(np.float64).ravel()))
     assert abs(lhs - rhs) <= 1e-5 * np.linalg.norm(gx.ravel()) * np.linalg.norm(r.ravel())
+
+
+@pytest.mark.parametrize("mesh", [SMALL_MESHES[0], SMALL_MESHES[3], SMALL_MESHES[5], (64, 1, 3, 10.0, 10.0, 10.0, 2.0)])
+@pytest.mark.parametrize("comps", [capi.GRAV_GX | capi.GRAV_GY, ALL7_GXY_SANS_GZZ,
+                                   capi.GRAV_GZ | capi.GRAV_GX | capi.GRAV_GZZ])
+def test_first_derivatives_match_oracle(gravlib, orc, mesh, comps):
+    """gx, gy (alone and with the other components) through the whole path:
+    FP64 and FP32 forward and adjoint against the oracle."""
+    nx, ny, nz = mesh[:3]
+    rng = np.random.default_rng(nx * 7 + ny + comps)
+    rho = rng.uniform(-500, 500, (nz, ny, nx))
+    ref = orc.forward(mesh, comps, rho)
+    assert np.all(rel_errors(run_forward(mesh, comps, rho, fp64=True), ref, comps) <= TOL64)
+    assert np.all(rel_errors(run_forward(mesh, comps, rho.astype(np.float32), fp64=False), ref, comps) <= TOL32)
+    r = rng.normal(size=(len(capi.comp_list(comps)), ny, nx))
+    gref = orc.adjoint(mesh, comps, r)
+    for fp64, tol in ((True, TOL64), (False, TOL32)):
+        g = run_adjoint(mesh, comps, r, fp64=fp64)
+        assert np.linalg.norm(g - gref) <= tol * np.linalg.norm(gref), fp64
 
 
 def test_repeatable_and_stream_ordered(gravlib):
