@@ -20,11 +20,11 @@
 // FP64 throughout: the eight corner terms cancel to a few parts in 1e7 at
 // the far offsets of a 1024-cell mesh, so FP32 generation is unusable.
 //
-// One thread per offset (u, v) of the quadrant u, v >= 0.  It walks down the
-// layers keeping the four (x, y)-corner terms of the shared z-level in
-// registers (the bottom of layer n is the top of layer n + 1), and writes
-// the four mirrored offsets (+-u, +-v) using the component's parity under
-// reflection (Sec. 2.2), so the stored kernel is exactly even or odd.
+// One thread per offset (u, v) of the quadrant u, v >= 0, in tiles that
+// share their corner terms (see kernel_gen below).  Walking down the layers,
+// each thread writes the four mirrored offsets (+-u, +-v) using the
+// component's parity under reflection (Sec. 2.2), so the stored kernel is
+// exactly even or odd.
 #include "grav_internal.h"
 
 namespace grav {
@@ -57,59 +57,82 @@ __device__ __forceinline__ void corner_terms(double x, double y, double z, unsig
     }
 }
 
-template <int NC>
-__global__ void kernel_gen(Geometry g, unsigned comps, int n0, int n1, int mode, int px, int py, double* __restrict__ out) {
-    const int u = blockIdx.x * blockDim.x + threadIdx.x;
-    const int v = blockIdx.y;
-    if (u >= g.nx || v >= g.ny) return;
-    const double xs[2] = {(0.5 - u) * g.dx, -(0.5 + u) * g.dx};
-    const double ys[2] = {(0.5 - v) * g.dy, -(0.5 + v) * g.dy};
+// Offsets per CTA: a kGenTX x kGenTY tile of the quadrant.  Neighbouring
+// offsets share prism corners (the far x-corner of offset u is the near one
+// of u + 1), so the CTA evaluates the corner terms of its (kGenTX + 1) x
+// (kGenTY + 1) corners once per z-level into shared memory (two levels kept:
+// the bottom of layer n is the top of layer n + 1) and every thread forms
+// its offset's kernel values from its eight corners.  The FP64 work per
+// offset and level drops from four corner evaluations to about 1.2.
+constexpr int kGenTX = 32, kGenTY = 8;
 
-    double top[4][NC];
-    {
-        const double z = -g.h - n0 * g.dz;
+template <int NC>
+__global__ void __launch_bounds__(kGenTX * kGenTY)
+    kernel_gen(Geometry g, unsigned comps, int n0, int n1, int mode, int px, int py, double* __restrict__ out) {
+    constexpr int CX = kGenTX + 1, CY = kGenTY + 1, NCOR = CX * CY, NT = kGenTX * kGenTY;
+    __shared__ double F[2][CY][CX][NC];  // corner terms of two z-levels
+    const int tx = threadIdx.x, ty = threadIdx.y, tid = ty * kGenTX + tx;
+    const int u0 = blockIdx.x * kGenTX, v0 = blockIdx.y * kGenTY;
+    const int u = u0 + tx, v = v0 + ty;
+
+    // corner terms of z-level z into buffer buf: corner (cu, cv) sits at
+    // x = (1/2 - cu) dx, y = (1/2 - cv) dy (station at the origin)
+    auto level = [&](int buf, double z) {
+        for (int e = tid; e < NCOR; e += NT) {
+            const int cy = e / CX, cx = e - cy * CX;
+            const int cu = u0 + cx, cv = v0 + cy;
+            double t[NC];
+            if (cu <= g.nx && cv <= g.ny) {
+                corner_terms<NC>((0.5 - cu) * g.dx, (0.5 - cv) * g.dy, z, comps, t);
+            } else {
 #pragma unroll
-        for (int ij = 0; ij < 4; ++ij) corner_terms(xs[ij >> 1], ys[ij & 1], z, comps, top[ij]);
-    }
+                for (int c = 0; c < NC; ++c) t[c] = 0.0;
+            }
+#pragma unroll
+            for (int c = 0; c < NC; ++c) F[buf][cy][cx][c] = t[c];
+        }
+    };
+
     const int nzc = n1 - n0;
     const int wx = 2 * g.nx - 1, wy = 2 * g.ny - 1;
+    int cur = 0;
+    level(cur, -g.h - n0 * g.dz);
     for (int n = n0; n < n1; ++n) {
-        double bot[4][NC];
-        const double z = -g.h - (n + 1) * g.dz;
+        level(cur ^ 1, -g.h - (n + 1) * g.dz);
+        __syncthreads();
+        if (u < g.nx && v < g.ny) {
 #pragma unroll
-        for (int ij = 0; ij < 4; ++ij) corner_terms(xs[ij >> 1], ys[ij & 1], z, comps, bot[ij]);
-#pragma unroll
-        for (int c = 0; c < NC; ++c) {
-            if (!(comps & (1u << c))) continue;
-            const int s = __popc(comps & ((1u << c) - 1u));  // output slot of component c
-            // mu_ijk: +1 for the bottom z-level when i + j is even
-            const double d00 = bot[0][c] - top[0][c];
-            const double d01 = bot[1][c] - top[1][c];
-            const double d10 = bot[2][c] - top[2][c];
-            const double d11 = bot[3][c] - top[3][c];
-            const double K = kUpsilon * ((d00 - d01) - (d10 - d11));
-            for (int mu = 0; mu < (u > 0 ? 2 : 1); ++mu) {
-                for (int mv = 0; mv < (v > 0 ? 2 : 1); ++mv) {
-                    double val = K;
-                    if (mu && odd_u(c)) val = -val;
-                    if (mv && odd_v(c)) val = -val;
-                    if ((u == 0 && odd_u(c)) || (v == 0 && odd_v(c))) val = 0.0;
-                    const int U = mu ? -u : u, V = mv ? -v : v;
-                    size_t idx;
-                    if (mode == 0) {
-                        const int a = (px - U) & (px - 1), b = (py - V) & (py - 1);
-                        idx = (((size_t)s * nzc + (n - n0)) * py + b) * px + a;
-                    } else {
-                        idx = (((size_t)s * g.nz + n) * wy + (V + g.ny - 1)) * wx + (U + g.nx - 1);
+            for (int c = 0; c < NC; ++c) {
+                if (!(comps & (1u << c))) continue;
+                const int s = __popc(comps & ((1u << c) - 1u));  // output slot of component c
+                // mu_ijk: +1 for the bottom z-level when i + j is even; corners
+                // (u + i, v + j)
+                const double d00 = F[cur ^ 1][ty][tx][c] - F[cur][ty][tx][c];
+                const double d01 = F[cur ^ 1][ty + 1][tx][c] - F[cur][ty + 1][tx][c];
+                const double d10 = F[cur ^ 1][ty][tx + 1][c] - F[cur][ty][tx + 1][c];
+                const double d11 = F[cur ^ 1][ty + 1][tx + 1][c] - F[cur][ty + 1][tx + 1][c];
+                const double K = kUpsilon * ((d00 - d01) - (d10 - d11));
+                for (int mu = 0; mu < (u > 0 ? 2 : 1); ++mu) {
+                    for (int mv = 0; mv < (v > 0 ? 2 : 1); ++mv) {
+                        double val = K;
+                        if (mu && odd_u(c)) val = -val;
+                        if (mv && odd_v(c)) val = -val;
+                        if ((u == 0 && odd_u(c)) || (v == 0 && odd_v(c))) val = 0.0;
+                        const int U = mu ? -u : u, V = mv ? -v : v;
+                        size_t idx;
+                        if (mode == 0) {
+                            const int a = (px - U) & (px - 1), b = (py - V) & (py - 1);
+                            idx = (((size_t)s * nzc + (n - n0)) * py + b) * px + a;
+                        } else {
+                            idx = (((size_t)s * g.nz + n) * wy + (V + g.ny - 1)) * wx + (U + g.nx - 1);
+                        }
+                        out[idx] = val;
                     }
-                    out[idx] = val;
                 }
             }
         }
-#pragma unroll
-        for (int ij = 0; ij < 4; ++ij)
-#pragma unroll
-            for (int c = 0; c < NC; ++c) top[ij][c] = bot[ij][c];
+        __syncthreads();  // the next level overwrites this level's top buffer
+        cur ^= 1;
     }
 }
 
@@ -117,13 +140,13 @@ __global__ void kernel_gen(Geometry g, unsigned comps, int n0, int n1, int mode,
 
 cudaError_t launch_kernel_gen(const Geometry& g, unsigned comps, int n0, int n1, int mode, int px, int py,
                               double* out, cudaStream_t s) {
-    const int bx = 64;
-    dim3 grid((g.nx + bx - 1) / bx, g.ny);
+    const dim3 block(kGenTX, kGenTY);
+    const dim3 grid((g.nx + kGenTX - 1) / kGenTX, (g.ny + kGenTY - 1) / kGenTY);
     comps &= kCompBits;
     if (comps & (GRAV_GX | GRAV_GY))
-        kernel_gen<9><<<grid, bx, 0, s>>>(g, comps, n0, n1, mode, px, py, out);
+        kernel_gen<9><<<grid, block, 0, s>>>(g, comps, n0, n1, mode, px, py, out);
     else
-        kernel_gen<7><<<grid, bx, 0, s>>>(g, comps, n0, n1, mode, px, py, out);
+        kernel_gen<7><<<grid, block, 0, s>>>(g, comps, n0, n1, mode, px, py, out);
     return cudaGetLastError();
 }
 
