@@ -20,6 +20,14 @@
 // ahead, in registers.  The spectra value of the Nyquist row (one per
 // component, used by one thread of the even-ky CTA) rides in the spare tail
 // of the layer's F slot.  Every wait is bounded.
+//
+// The odd-ky CTA transforms the folded column x[m] W_Py^m (Py = 2N).  With
+// m = 32 n1 + n2 the fold factor is W_64^n1 W_2048^n2: the first factor is a
+// constant of register n1, the second is constant over n1 and so moves past
+// the first 32-point pass into the transpose twiddles, t2 = W_2048^((2 k1 +
+// r) n2).  The inverse transform cancels the extra W_2048^-n2 that these
+// twiddles carry by scaling its input by W_2048^n2 first, and unfolds its
+// output y = n2 + 32 k by W_2048^-n2 W_64^-k.
 #pragma once
 #include "async_copy.cuh"
 #include "fft_block.cuh"
@@ -46,7 +54,7 @@ struct WfShape {
 struct WfSmem {
     int df;
     uint32_t x_bytes, s_bytes, f_bytes;
-    uint32_t f_off, tw_off, t2_off, cmp_off, bar_off, flag_off, total;
+    uint32_t f_off, t2_off, cmp_off, bar_off, flag_off, total;
 };
 
 template <int NC>
@@ -63,8 +71,7 @@ __global__ void __maxnreg__(WfShape::REGS)
     extern __shared__ __align__(128) unsigned char smem[];
     unsigned char* xring = smem;
     C* fring = reinterpret_cast<C*>(smem + L.f_off);
-    C* tws = reinterpret_cast<C*>(smem + L.tw_off);  // fold twiddles W_Py^m, m < N
-    C* t2 = reinterpret_cast<C*>(smem + L.t2_off);   // W_1024^(n2 k1) at [k1][n2]
+    C* t2 = reinterpret_cast<C*>(smem + L.t2_off);  // W_2048^((2 k1 + r) n2) at [k1][n2]
     float* cmp = reinterpret_cast<float*>(smem + L.cmp_off);  // Kahan corrections [c][j][q]
     uint64_t* bars = reinterpret_cast<uint64_t*>(smem + L.bar_off);
     uint64_t* xfull = bars;
@@ -90,9 +97,8 @@ __global__ void __maxnreg__(WfShape::REGS)
         fence_mbar_init();
     }
     for (int e = tid; e < N; e += NT) {
-        tws[e] = tw[e << a.tw_shift_p];
         const int k1 = e >> 5, n2 = e & 31;
-        t2[e] = tw[((k1 * n2) & (N - 1)) << a.tw_shift_n];
+        t2[e] = tw[(((2 * k1 + r) * n2) & (2 * N - 1)) << a.tw_shift_p];
     }
     for (int e = tid; e < 4 * NC * J; e += NT) cmp[e] = 0.f;
     __syncthreads();
@@ -139,10 +145,7 @@ __global__ void __maxnreg__(WfShape::REGS)
             for (int n1 = 0; n1 < 32; ++n1) {
                 const int m = 32 * n1 + lane;
                 C v = make_float2(0.f, 0.f);
-                if (m < ny) {
-                    v = xs[m];
-                    if (r) v = cmul(v, tws[m]);  // fold for ky parity r
-                }
+                if (m < ny) v = xs[m];
                 u[n1] = v;
             }
             __syncwarp();  // every lane's reads of X slot f are done
@@ -154,6 +157,10 @@ __global__ void __maxnreg__(WfShape::REGS)
                     pending = n + FW;
                 }
                 if (n + PF < nz) bulk_prefetch_l2(Sk + (size_t)(n + PF) * S_ROW, L.s_bytes);
+            }
+            if (r) {
+#pragma unroll
+                for (int n1 = 0; n1 < 32; ++n1) u[n1] = tw64(u[n1], n1);  // fold factor W_64^n1
             }
             C* fb = fring + sf * FS;
             warp_fft1024<false>(u, fb, t2, lane);
@@ -177,15 +184,26 @@ __global__ void __maxnreg__(WfShape::REGS)
 #pragma unroll
             for (int n1 = 0; n1 < 32; ++n1) u[n1] = fb[32 * n1 + lane];
             __syncwarp();
+            if (r) {
+                const C w = __ldg(tw + (lane << a.tw_shift_p));  // W_2048^n2, n2 = lane
+#pragma unroll
+                for (int n1 = 0; n1 < 32; ++n1) u[n1] = cmul(u[n1], w);
+            }
             warp_fft1024<true>(u, fb, t2, lane);
             C* dst = Y + ((size_t)(r * a.kx_count + kx) * a.ncomp + c) * a.ny_pad;
+            if (r) {
+                // unfold: W_2048^-y with y = lane + 32 k is W_2048^-lane W_64^-k
+                const C w = cconj(__ldg(tw + (lane << a.tw_shift_p)));
 #pragma unroll
-            for (int j = 0; j < 32; ++j) {
-                const int y = lane + 32 * bitrev5(j);
-                if (y < ny) {
-                    C v = u[j];
-                    if (r) v = cmul(v, cconj(tws[y]));
-                    dst[y] = v;
+                for (int j = 0; j < 32; ++j) {
+                    const int y = lane + 32 * bitrev5(j);
+                    if (y < ny) dst[y] = tw64(cmul(u[j], w), 64 - bitrev5(j));
+                }
+            } else {
+#pragma unroll
+                for (int j = 0; j < 32; ++j) {
+                    const int y = lane + 32 * bitrev5(j);
+                    if (y < ny) dst[y] = u[j];
                 }
             }
         }
@@ -209,9 +227,9 @@ __global__ void __maxnreg__(WfShape::REGS)
         float sv[NC];
 #pragma unroll
         for (int c = 0; c < NC; ++c) sv[c] = nz > 0 ? __ldg(Sq + c * JP) : 0.f;
+        int sf = 0, wrap = 0;  // F slot of layer n (n % df) and n / df, stepped with n
         for (int n = 0; n < nz; ++n) {
-            const int sf = n % L.df;
-            if (!ws_wait(&ffull[sf], (uint32_t)((n / L.df) & 1), abort)) {
+            if (!ws_wait(&ffull[sf], (uint32_t)(wrap & 1), abort)) {
                 failed = true;
                 break;
             }
@@ -226,6 +244,10 @@ __global__ void __maxnreg__(WfShape::REGS)
                 part[c][3] += s2 * v2.y;
             }
             mbar_arrive(&fempty[sf]);
+            if (++sf == L.df) {
+                sf = 0;
+                ++wrap;
+            }
             if (n + 1 < nz) {
                 const float* row = Sq + (size_t)(n + 1) * S_ROW;
 #pragma unroll
@@ -285,8 +307,7 @@ inline WfSmem wf_smem(int ny_pad, int ncomp, int jp, int nc_inst, int max_bytes)
         WfSmem l = L;
         l.df = df;
         l.f_off = (uint32_t)(WfShape::DX * L.x_bytes + 127) & ~127u;
-        l.tw_off = l.f_off + df * L.f_bytes;
-        l.t2_off = l.tw_off + WfShape::N * sizeof(float2);
+        l.t2_off = l.f_off + df * L.f_bytes;
         l.cmp_off = l.t2_off + WfShape::N * sizeof(float2);
         l.bar_off = l.cmp_off + 4 * nc_inst * WfShape::J * sizeof(float);
         l.flag_off = l.bar_off + (WfShape::DX + 2 * df) * 8;
