@@ -47,8 +47,8 @@ COMPS = 63
 NCOMP = 6
 FALLBACK_HBM_GBS = 6800.0
 PROFILE_SUMMARY = os.path.join(ROOT, "profiles", "forward_columns_grf1024.md")
-KERNEL_SOURCES = ("fft_block.cuh", "spectral.cuh", "spectral_ws.cuh", "spectral_wf.cuh", "spectral_launch.cuh",
-                  "async_copy.cuh", "col_fwd_f32.cu", "grav_internal.h")
+KERNEL_SOURCES = ("fft_block.cuh", "spectral.cuh", "spectral_ws.cuh", "spectral_wf.cuh", "warp_fft.cuh",
+                  "spectral_launch.cuh", "async_copy.cuh", "col_fwd_f32.cu", "grav_internal.h")
 
 
 def parse():

@@ -146,6 +146,14 @@ cudaError_t launch_row_c2r(int log_p, const void* in0, const void* in1, int I, i
                            R* out, size_t out_stride, int l_out, const void* tw, int log_t,
                            cudaStream_t s, Batch b = Batch());
 
+// Forward column stage for 512-point FP32 columns (Py = 1024) with both ky
+// parities of a column in one CTA and two transforms per warp
+// (col_fwd512_f32.cu).  Same arguments and layouts as the column launchers
+// below; cudaErrorNotSupported when the sizes do not fit it (ny_pad > 512,
+// more than 7 components) or err is null, and the caller takes another kernel.
+cudaError_t launch_forward_wf512(const ColumnArgs& a, const void* X, const float* spec, void* Y, const void* tw,
+                                 int* err, cudaStream_t s, Batch b);
+
 // Adjoint inverse rows from the tiled column output (ColumnArgs::z_tiled):
 // in_r[n][y / 8][kx][8] (swizzled as described there) for r = 0, 1 (in1 = in0 + one half), summed, kx
 // in [0, 1024]; out row (n, y) at out + (n * ny + y) * out_stride, first

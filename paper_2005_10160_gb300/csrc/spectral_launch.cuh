@@ -24,6 +24,12 @@ cudaError_t forward_impl(const ColumnArgs& a, const void* X, const R* spec, void
             return cudaGetLastError();
         }
     }
+    if constexpr (sizeof(R) == 4 && LOGN == 9) {
+        // 512-point FP32 columns: both parities of a column per CTA, two
+        // transforms per warp (col_fwd512_f32.cu)
+        const cudaError_t e = launch_forward_wf512(a, X, (const float*)spec, Y, tw, err, s, b);
+        if (e != cudaErrorNotSupported) return e;
+    }
     if constexpr (sizeof(R) == 4 && (LOGN == 9 || LOGN == 10)) {
         // large FP32 transforms: the warp-specialised kernel
         const WsSmem W = ws_smem<LOGN>(a.ny_pad, a.ncomp, a.jp, NC, kMaxSmemOptin);

@@ -118,4 +118,53 @@ __device__ __forceinline__ void warp_fft1024(float2 (&u)[32], float2* tr, const 
     dft32<INV>(u);
 }
 
+__host__ __device__ constexpr int bitrev4(int j) { return ((j & 1) << 3) | ((j & 2) << 1) | ((j & 4) >> 1) | ((j & 8) >> 3); }
+
+// 16-point DFT of u[OFF .. OFF + 15] in registers, radix-2 decimation in
+// frequency (W_16^k = W_32^(2k)): natural order in, u[OFF + j] = X[bitrev4(j)]
+// out.
+template <bool INV, int OFF> __device__ __forceinline__ void dft16(float2 (&u)[32]) {
+#pragma unroll
+    for (int h = 8; h >= 1; h >>= 1) {
+#pragma unroll
+        for (int b = 0; b < 16; b += 2 * h) {
+#pragma unroll
+            for (int i = 0; i < h; ++i) {
+                const float2 a = u[OFF + b + i], c = u[OFF + b + i + h];
+                u[OFF + b + i] = make_float2(a.x + c.x, a.y + c.y);
+                u[OFF + b + i + h] = tw32<INV>(make_float2(a.x - c.x, a.y - c.y), 2 * i * (8 / h));
+            }
+        }
+    }
+}
+
+// Two 512-point FFTs by one warp, 512 = 16 x 32: x[32 n1 + n2] (n1 < 16) ->
+// 16-point DFTs over n1 (lane n2) -> twiddle -> transpose -> 32-point DFTs
+// over n2.  In: u[n1] = a[32 n1 + lane], u[16 + n1] = b[32 n1 + lane].  Out:
+// lane L holds transform L / 16 (0: a, 1: b) at k1 = L % 16, u[j] = X[k1 +
+// 16 bitrev5(j)].  t2[(16 h + k1) 32 + lane] is the twiddle of transform h
+// at (k1, n2 = lane), W_512^(n2 k1) for a plain pair of transforms (a caller
+// may fold a factor constant over n1 into it).  tr: the warp's 32 x 33
+// transpose area, free for the caller afterwards.
+template <bool INV>
+__device__ __forceinline__ void warp_fft512x2(float2 (&u)[32], float2* tr, const float2* t2, int lane) {
+    dft16<INV, 0>(u);
+    dft16<INV, 16>(u);
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+#pragma unroll
+        for (int j = 0; j < 16; ++j) {
+            const int K = 16 * h + bitrev4(j);
+            float2 w = t2[K * 32 + lane];
+            if (INV) w.y = -w.y;
+            tr[K * 33 + lane] = cmul(u[16 * h + j], w);
+        }
+    }
+    __syncwarp();
+#pragma unroll
+    for (int n2 = 0; n2 < 32; ++n2) u[n2] = tr[lane * 33 + n2];
+    __syncwarp();
+    dft32<INV>(u);
+}
+
 }  // namespace grav

@@ -204,12 +204,10 @@ WIDE_MESHES = [
 ]
 
 
-@pytest.mark.parametrize("mesh", WIDE_MESHES)
-@pytest.mark.parametrize("comps", [ALL7, 0x3F, capi.GRAV_GZ, capi.GRAV_GXY | capi.GRAV_GYZ, ALL7_GXY_SANS_GZZ])
-def test_forward_fp32_wide_columns(gravlib, orc, mesh, comps):
-    """FP32 forward on 2048-point columns: against the oracle at sampled
-    stations, and against the FP64 spectral path at every station; the FP32
-    adjoint against the FP64 adjoint at every cell."""
+def check_fp32_columns(orc, mesh, comps):
+    """FP32 forward against the oracle at sampled stations and against the
+    FP64 spectral path at every station; the FP32 adjoint against the FP64
+    adjoint at every cell."""
     nx, ny, nz = mesh[:3]
     rng = np.random.default_rng(nx * 1000 + ny + nz)
     rho = rng.uniform(-300, 300, (nz, ny, nx))
@@ -221,11 +219,37 @@ def test_forward_fp32_wide_columns(gravlib, orc, mesh, comps):
     assert np.all(rel_errors(got32[:, st], ref, comps) <= TOL32)
     assert np.all(rel_errors(got64[:, st], ref, comps) <= TOL64)
     assert np.all(rel_errors(got32, got64, comps) <= TOL32)
-    # the adjoint on the same columns: FP32 against the FP64 spectral path
     r = rng.normal(size=(len(capi.comp_list(comps)), ny, nx))
     g32 = run_adjoint(mesh, comps, r, fp64=False).reshape(-1)
     g64 = run_adjoint(mesh, comps, r, fp64=True).reshape(-1)
     assert np.linalg.norm(g32 - g64) <= TOL32 * np.linalg.norm(g64)
+
+
+@pytest.mark.parametrize("mesh", WIDE_MESHES)
+@pytest.mark.parametrize("comps", [ALL7, 0x3F, capi.GRAV_GZ, capi.GRAV_GXY | capi.GRAV_GYZ, ALL7_GXY_SANS_GZZ])
+def test_forward_fp32_wide_columns(gravlib, orc, mesh, comps):
+    """2048-point columns (1024-point warp transforms): forward and adjoint."""
+    check_fp32_columns(orc, mesh, comps)
+
+
+# Meshes with 257 <= ny <= 512: Py = 1024, so the FP32 forward runs the
+# 512-point column kernel with both ky parities in one CTA and two transforms
+# per warp (ragged ny_pad, fewer layers than FFT warps, enough layers to wrap
+# every ring and cross a compensated block); eight components take the
+# fallback kernel.
+MID_MESHES = [
+    (3, 512, 20, 10.0, 10.0, 10.0, 2.0),
+    (5, 257, 9, 20.0, 15.0, 10.0, 3.0),
+    (2, 300, 1, 10.0, 10.0, 10.0, 1.0),
+    (33, 420, 40, 20.0, 20.0, 15.0, 4.0),
+]
+
+
+@pytest.mark.parametrize("mesh", MID_MESHES)
+@pytest.mark.parametrize("comps", [ALL7, 0x3F, capi.GRAV_GZ, capi.GRAV_GXY | capi.GRAV_GYZ, ALL7_GXY_SANS_GZZ])
+def test_forward_fp32_mid_columns(gravlib, orc, mesh, comps):
+    """1024-point columns (512-point transforms, two per warp): forward and adjoint."""
+    check_fp32_columns(orc, mesh, comps)
 
 
 # Meshes with 513 <= nx <= 1024: Px = 2048, so the FP32 row stages run the
