@@ -153,6 +153,11 @@ cudaError_t launch_row_c2r(int log_p, const void* in0, const void* in1, int I, i
 // more than 7 components) or err is null, and the caller takes another kernel.
 cudaError_t launch_forward_wf512(const ColumnArgs& a, const void* X, const float* spec, void* Y, const void* tw,
                                  int* err, cudaStream_t s, Batch b);
+// The adjoint counterpart (col_adj512_f32.cu), writing the untiled column
+// output; cudaErrorNotSupported when ny_pad > 512, more than 8 components,
+// err is null or a.z_tiled is set.
+cudaError_t launch_adjoint_wf512(const ColumnArgs& a, const void* Xr, const float* spec, void* Z, const void* tw,
+                                 int* err, cudaStream_t s, Batch b);
 
 // Adjoint inverse rows from the tiled column output (ColumnArgs::z_tiled):
 // in_r[n][y / 8][kx][8] (swizzled as described there) for r = 0, 1 (in1 = in0 + one half), summed, kx

@@ -127,6 +127,12 @@ cudaError_t adjoint_impl(const ColumnArgs& a, const void* Xr, const R* spec, voi
             }
         }
     }
+    if constexpr (sizeof(R) == 4 && LOGN == 9) {
+        // 512-point FP32 columns: both parities of a column per CTA, two
+        // transforms per warp (col_adj512_f32.cu)
+        const cudaError_t e = launch_adjoint_wf512(a, Xr, (const float*)spec, Z, tw, err, s, b);
+        if (e != cudaErrorNotSupported) return e;
+    }
     constexpr auto k = adjoint_column_kernel<R, LOGN, CPG>;
     const size_t smem = column_smem_bytes<R>(LOGN);
     cudaError_t e = ensure_smem_limit<k>();

@@ -176,12 +176,15 @@ def test_boxes256_fp64_vs_oracle_and_superposition(gravlib, orc):
     assert np.all(err2 <= TOL64), err2
 
 
-def test_dot_product_adjoint(gravlib):
-    """<G x, y> = <x, G^T y> on a ragged mesh, FP64 and FP32."""
-    mesh = (45, 23, 7, 20.0, 25.0, 10.0, 3.0)
+@pytest.mark.parametrize("mesh", [(45, 23, 7, 20.0, 25.0, 10.0, 3.0),     # 64-point columns
+                                  (21, 300, 11, 20.0, 15.0, 10.0, 3.0),   # 512-point, two per warp
+                                  (9, 600, 10, 20.0, 15.0, 10.0, 3.0)])   # 1024-point warp transforms
+def test_dot_product_adjoint(gravlib, mesh):
+    """<G x, y> = <x, G^T y> on ragged meshes, FP64 and FP32."""
+    nx, ny, nz = mesh[:3]
     rng = np.random.default_rng(11)
-    x = rng.normal(size=(7, 23, 45))
-    y = rng.normal(size=(7, 23, 45))
+    x = rng.normal(size=(nz, ny, nx))
+    y = rng.normal(size=(7, ny, nx))
     for fp64, tol in ((True, 1e-12), (False, 1e-5)):
         dt = torch.float64 if fp64 else torch.float32
         with Plan(mesh, ALL7, fp64=fp64) as plan:
