@@ -138,10 +138,10 @@ __global__ void __maxnreg__(AwShape::REGS)
         if (q == 0)
             for (int n = 0; n < PF && n < nz; ++n) bulk_prefetch_l2(Sk + (size_t)n * S_ROW, S_ROW * sizeof(float));
         if (nz > 0) load(0);
+        int sz = 0, wrap = 0;  // ring slot of layer n (n % dz) and n / dz, stepped with n
         for (int n = 0; n < nz; ++n) {
-            const int sz = n % L.dz;
             if (q == 0 && n + PF < nz) bulk_prefetch_l2(Sk + (size_t)(n + PF) * S_ROW, S_ROW * sizeof(float));
-            if (n >= L.dz && !ws_wait(&zempty[sz], (uint32_t)((n / L.dz - 1) & 1), abort)) {
+            if (n >= L.dz && !ws_wait(&zempty[sz], (uint32_t)((wrap - 1) & 1), abort)) {
                 failed = true;
                 break;
             }
@@ -169,6 +169,10 @@ __global__ void __maxnreg__(AwShape::REGS)
             zb[k1] = z1;
             zb[k2] = z2;
             mbar_arrive(&zfull[sz]);
+            if (++sz == L.dz) {
+                sz = 0;
+                ++wrap;
+            }
         }
         if (cta_sync_or(failed || *abort)) {
             if (tid == 0) atomicExch(err, 1);
