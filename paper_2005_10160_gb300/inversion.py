@@ -114,7 +114,9 @@ def cgls(plan: Plan, d: torch.Tensor, w: torch.Tensor, lam: float, iters: int = 
 
     d: data [ncomp][ny][nx]; w: data weights broadcastable to d (1/sigma_c as
     [ncomp, 1, 1]); lam: Tikhonov weight on ||W_m m||^2; iters: iterations.
-    Returns the model m = W_m^-1 x and the objective after every iteration."""
+    plan: anything with .mesh, .forward and .adjoint on d's device (a Plan).
+    Returns the model m = W_m^-1 x and the objective after every iteration;
+    ms_per_iteration is timed with CUDA events when d is on a GPU (else nan)."""
     wm = depth_weights(plan.mesh, beta, device=d.device, dtype=d.dtype)
 
     def A(x):
@@ -131,8 +133,10 @@ def cgls(plan: Plan, d: torch.Tensor, w: torch.Tensor, lam: float, iters: int = 
     gamma = _dot(s, s)
     objectives = [_dot(r, r)]
     models = []
-    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    e0.record()
+    timed = d.is_cuda
+    if timed:
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
     for _ in range(iters):
         if gamma == 0.0:
             objectives.append(objectives[-1])
@@ -151,9 +155,11 @@ def cgls(plan: Plan, d: torch.Tensor, w: torch.Tensor, lam: float, iters: int = 
         objectives.append(_dot(r, r) + lam * _dot(x, x))
         if keep_models:
             models.append((x / wm).clone())
-    e1.record()
-    torch.cuda.synchronize()
-    ms = e0.elapsed_time(e1) / max(1, iters)
+    ms = float("nan")
+    if timed:
+        e1.record()
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / max(1, iters)
     return CGLSResult(m=x / wm, models=models, objectives=objectives, iterations=iters, lam=lam,
                       ms_per_iteration=ms)
 
