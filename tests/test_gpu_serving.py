@@ -126,11 +126,13 @@ def test_request_beyond_the_budget_fails_cleanly(gravlib):
 
 @pytest.mark.parametrize("mesh", [MESHES[2], W.Mesh(6, 600, 10, 20.0, 20.0, 10.0, 5.0),
                                   W.Mesh(520, 9, 5, 20.0, 20.0, 10.0, 5.0),
-                                  W.Mesh(520, 528, 3, 20.0, 20.0, 10.0, 5.0)])
+                                  W.Mesh(520, 528, 3, 20.0, 20.0, 10.0, 5.0),
+                                  W.Mesh(12, 300, 7, 20.0, 20.0, 10.0, 5.0)])
 def test_batch_runner_matches_single_calls(gravlib, mesh):
     """grav_forward_batch / grav_adjoint_batch with a caller workspace equal
     per-request plain calls (the second mesh runs 2048-point columns, the
-    third 2048-point rows, the fourth both, with the tiled adjoint)."""
+    third 2048-point rows, the fourth both, with the tiled adjoint, the fifth
+    1024-point columns with two 512-point transforms per warp)."""
     rng = np.random.default_rng(8)
     with Plan(mesh, capi.GRAV_ALL6) as plan:
         run = BatchRunner(plan)
