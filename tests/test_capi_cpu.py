@@ -64,3 +64,49 @@ def test_null_plan_and_buffers_are_rejected(gravlib):
     assert L.grav_forward_static_scratch(None, None, None, None) == capi.GRAV_EINVAL
     rc, _ = capi.grav_selftest_bounded_wait(0.0)
     assert rc == capi.GRAV_EINVAL
+
+
+def _c_values(tmp_path, body):
+    """Compile a C program against include/grav.h with gcc and return what it
+    prints as name -> integer."""
+    import shutil
+    import subprocess
+
+    gcc = shutil.which("gcc")
+    if gcc is None:
+        pytest.skip("gcc not available")
+    src = tmp_path / "abi.c"
+    src.write_text('#include <stddef.h>\n#include <stdio.h>\n#include "grav.h"\nint main(void) {\n' + body +
+                   "return 0; }\n")
+    exe = tmp_path / "abi"
+    subprocess.run([gcc, "-std=c99", "-I", os.path.dirname(HEADER), str(src), "-o", str(exe)], check=True)
+    out = subprocess.run([str(exe)], check=True, capture_output=True, text=True).stdout
+    return {k: int(v) for k, v in (line.split() for line in out.splitlines())}
+
+
+CONSTANTS = ["GRAV_GZ", "GRAV_GXX", "GRAV_GXY", "GRAV_GXZ", "GRAV_GYY", "GRAV_GYZ", "GRAV_GZZ", "GRAV_GX", "GRAV_GY",
+             "GRAV_ALL6", "GRAV_FP64_SPECTRAL", "GRAV_OK", "GRAV_EINVAL", "GRAV_ENOMEM", "GRAV_ECUDA",
+             "GRAV_ETIMEOUT", "GRAV_MAX_NX", "GRAV_MAX_NY", "GRAV_STATIC_SCRATCH_BYTES"]
+
+
+def test_binding_constants_equal_the_header(tmp_path):
+    """Every constant of include/grav.h, as a C compiler sees it, equals the
+    Python binding's."""
+    body = "".join(f'printf("{n} %lld\\n", (long long)({n}));\n' for n in CONSTANTS)
+    c = _c_values(tmp_path, body)
+    for n in CONSTANTS:
+        assert c[n] == getattr(capi, n), n
+    assert capi.GRAV_COMP_BITS == c["GRAV_GZ"] | c["GRAV_GXX"] | c["GRAV_GXY"] | c["GRAV_GXZ"] | c["GRAV_GYY"] | \
+        c["GRAV_GYZ"] | c["GRAV_GZZ"] | c["GRAV_GX"] | c["GRAV_GY"]
+
+
+def test_plan_info_struct_layout_equals_the_header(tmp_path):
+    """grav_plan_info_t has the same size and field offsets in C and in the
+    ctypes mirror the binding passes to grav_plan_info."""
+    fields = [f[0] for f in capi.grav_plan_info_t._fields_]
+    body = 'printf("sizeof %zu\\n", sizeof(grav_plan_info_t));\n' + "".join(
+        f'printf("{f} %zu\\n", offsetof(grav_plan_info_t, {f}));\n' for f in fields)
+    c = _c_values(tmp_path, body)
+    assert c["sizeof"] == ctypes.sizeof(capi.grav_plan_info_t)
+    for f in fields:
+        assert c[f] == getattr(capi.grav_plan_info_t, f).offset, f
