@@ -110,3 +110,40 @@ def test_plan_info_struct_layout_equals_the_header(tmp_path):
     assert c["sizeof"] == ctypes.sizeof(capi.grav_plan_info_t)
     for f in fields:
         assert c[f] == getattr(capi.grav_plan_info_t, f).offset, f
+
+
+def _prototypes():
+    """name -> (return type, [parameter types]) of every function in grav.h."""
+    text = re.sub(r"/\*.*?\*/", "", open(HEADER).read(), flags=re.S)
+    protos = {}
+    for ret, name, params in re.findall(r"([A-Za-z_][\w \t\*]*?)\s*\b(grav_[a-z_0-9]+)\s*\(([^)]*)\)\s*;", text):
+        plist = [] if params.strip() in ("", "void") else [q.strip() for q in params.split(",")]
+        types = []
+        for q in plist:
+            # pointers and array parameters (which decay to pointers); else drop the name
+            types.append("pointer" if ("*" in q or "[" in q) else " ".join(q.split()[:-1]))
+        protos[name] = (" ".join(ret.replace("*", " * ").split()), types)
+    return protos
+
+
+def _kind(ctype):
+    if ctype is None:
+        return "void"
+    if ctype in (ctypes.c_void_p, ctypes.c_char_p) or issubclass(ctype, ctypes._Pointer):
+        return "pointer"
+    return {ctypes.c_int: "int", ctypes.c_uint: "unsigned", ctypes.c_double: "double",
+            ctypes.c_size_t: "size_t", ctypes.c_longlong: "long long"}[ctype]
+
+
+def test_binding_signatures_equal_the_header(gravlib):
+    """The ctypes argument and return types the binding sets match the
+    header's prototypes parameter by parameter (count and kind)."""
+    capi.lib()
+    protos = _prototypes()
+    assert sorted(protos) == sorted(capi.EXPORTED)
+    for name, (ret, params) in protos.items():
+        fn = getattr(gravlib, name)
+        want = ["unsigned" if t in ("unsigned", "unsigned int") else t for t in params]
+        assert [_kind(t) for t in fn.argtypes] == want, name
+        want_ret = "pointer" if "*" in ret else ret.replace("const ", "")
+        assert _kind(fn.restype) == want_ret, (name, ret)
