@@ -56,6 +56,51 @@ def test_paper_cube_matches_quadrature(orc, station):
         assert np.abs(got[idx] - ref[idx]).max() <= 1e-12 * scale, (idx, (got[idx] - ref[idx]) / scale)
 
 
+@pytest.mark.parametrize("station", [(25.0, 5.0, 5.0), (-12.0, 17.0, 3.0), (15.0, 15.0, 9.0), (5.0, 25.0, 0.5),
+                                     (30.0, -7.0, 12.0)])
+def test_closed_forms_hold_level_with_the_prism(orc, station):
+    """Stations beside the prism at depths inside its depth range (corners
+    on both sides of the station's z, where the atan terms change branch):
+    all nine closed forms still equal quadrature to 1e-12."""
+    box = (0.0, 10.0, 0.0, 10.0, 0.0, 10.0)
+    ref = prism_quadrature(station, box, nsub=8, order=16)
+    got = orc.prism(station, box)
+    for idx in ([0, 7, 8], [1, 2, 3, 4, 5, 6]):
+        scale = np.abs(ref[idx]).max()
+        assert np.abs(got[idx] - ref[idx]).max() <= 1e-12 * scale, (idx, (got[idx] - ref[idx]) / scale)
+
+
+@pytest.mark.parametrize("box", [(0.0, 10.0, 0.0, 10.0, 0.0, 10.0), (0.0, 20.0, 0.0, 12.0, 0.0, 7.0),
+                                 (-3.0, 4.0, 5.0, 9.0, 1.0, 2.5)])
+@pytest.mark.parametrize("frac", [(0.5, 0.5, 0.5), (0.2, 0.7, 0.4), (0.9, 0.1, 0.65), (0.33, 0.5, 0.95)])
+def test_interior_points_obey_poisson(orc, box, frac):
+    """Stations inside the prism (quadrature does not apply: the integrand
+    is singular there): the trace of the gradient tensor is -4 pi upsilon rho
+    (Poisson's equation instead of Laplace's), and the derivatives of gz by
+    fourth-order finite differences equal gxz, gyz and gzz."""
+    st = np.array([box[2 * i] + frac[i] * (box[2 * i + 1] - box[2 * i]) for i in range(3)])
+    g = orc.prism(tuple(st), box) / 6.672e-11  # per unit upsilon rho
+    assert abs(g[1] + g[4] + g[6] + 4 * np.pi) <= 1e-12 * 4 * np.pi
+    h = 1e-3 * min(box[1] - box[0], box[3] - box[2], box[5] - box[4])
+
+    def gz(p):
+        return orc.prism(tuple(p), box)[0] / 6.672e-11
+
+    for axis, comp in ((0, 3), (1, 5), (2, 6)):
+        e = np.zeros(3)
+        e[axis] = h
+        fd = (-gz(st + 2 * e) + 8 * gz(st + e) - 8 * gz(st - e) + gz(st - 2 * e)) / (12 * h)
+        assert abs(fd - g[comp]) <= 1e-9 * 4 * np.pi, (axis, fd, g[comp])
+
+
+def test_cube_centre_field(orc):
+    """At the centre of a cube every odd component vanishes and each diagonal
+    component is a third of -4 pi upsilon rho."""
+    g = orc.prism((5.0, 5.0, 5.0), (0.0, 10.0, 0.0, 10.0, 0.0, 10.0)) / 6.672e-11
+    assert np.allclose(g[[0, 2, 3, 5, 7, 8]], 0.0, atol=1e-13)
+    assert np.allclose(g[[1, 4, 6]], -4 * np.pi / 3, rtol=1e-13)
+
+
 @pytest.mark.parametrize("direction", [(1, 0.3, 2), (-2, 1, 1), (0.2, -0.1, 3), (3, 3, 0.5)])
 def test_far_field_point_mass_cube(orc, direction):
     """A cube has no quadrupole moment, so far away it acts as a point mass
