@@ -76,6 +76,10 @@ def _load():
             lib.orc_adjoint.restype = i
             lib.orc_gmatrix.argtypes = [i, i, i, d, d, d, d, u, p]
             lib.orc_gmatrix.restype = i
+            lib.orc_forward3d.argtypes = [i, i, i, d, d, d, u, p, i, p, p, i]
+            lib.orc_forward3d.restype = i
+            lib.orc_gmatrix3d.argtypes = [i, i, i, d, d, d, u, p]
+            lib.orc_gmatrix3d.restype = i
             _lib = lib
     return _lib
 
@@ -184,3 +188,40 @@ def box_field(mesh, comps: int, box_cells, density: float, stations=None) -> np.
         v = prism(((p + 0.5) * dx, (q + 0.5) * dy, -h), box)
         out[:, s] = v[lst] * density
     return out
+
+
+def forward3d(mesh, comps: int, rho: np.ndarray, stations=None, nthreads=None) -> np.ndarray:
+    """Equal-dimension variant (Sec. 2.2, Eqs. 10-11): direct summation with
+    a station at the centre of every cell.  mesh = (nx, ny, nz, dx, dy, dz,
+    h), h unused; rho is [nz][ny][nx]; ``stations`` an optional list of
+    station indices p + nx q + nx ny t.  Returns [ncomp][nz][ny][nx] (all
+    stations) or [ncomp][n_stations]."""
+    lib = _load()
+    nx, ny, nz, dx, dy, dz, _ = _geom(mesh)
+    rho = np.ascontiguousarray(rho, dtype=np.float64).reshape(nz, ny, nx)
+    full = stations is None
+    idx = np.arange(nx * ny * nz, dtype=np.int32) if full else np.ascontiguousarray(stations, dtype=np.int32)
+    nc = len(comp_list(comps))
+    out = np.zeros((nc, idx.size), dtype=np.float64)
+    rc = lib.orc_forward3d(nx, ny, nz, dx, dy, dz, comps, rho.ctypes.data_as(ctypes.c_void_p), int(idx.size),
+                           idx.ctypes.data_as(ctypes.c_void_p), out.ctypes.data_as(ctypes.c_void_p),
+                           int(nthreads or default_threads()))
+    if rc != 0:
+        raise ValueError("orc_forward3d: invalid arguments")
+    return out.reshape(nc, nz, ny, nx) if full else out
+
+
+def gmatrix3d(mesh, comps: int) -> np.ndarray:
+    """Equal-dimension variant: explicit G[c][i][j], station i at the centre
+    of cell i, for tiny meshes."""
+    lib = _load()
+    nx, ny, nz, dx, dy, dz, _ = _geom(mesh)
+    nc = len(comp_list(comps))
+    nm = nx * ny * nz
+    if nc * nm * nm > 50_000_000:
+        raise ValueError("gmatrix3d is for tiny meshes only")
+    G = np.zeros((nc, nm, nm), dtype=np.float64)
+    rc = lib.orc_gmatrix3d(nx, ny, nz, dx, dy, dz, comps, G.ctypes.data_as(ctypes.c_void_p))
+    if rc != 0:
+        raise ValueError("orc_gmatrix3d: invalid arguments")
+    return G

@@ -39,6 +39,11 @@
  * j = l + nx*m + nx*ny*n):
  *   cell (l, m, n) spans [l dx, (l+1) dx] x [m dy, (m+1) dy] x [n dz, (n+1) dz]
  *   station (p, q) sits at ((p + 1/2) dx, (q + 1/2) dy, -h), h > 0
+ *   In the equal-dimension variant (Sec. 2.2, Eqs. 10-11: data as
+ *   three-dimensional as the mesh) station (p, q, t) sits at the centre of
+ *   cell (p, q, t), index i = p + nx*q + nx*ny*t.  A cell centre is never on
+ *   a corner plane of any cell, so every term of the closed forms is
+ *   finite; at the station's own cell they give the interior field.
  *   upsilon = 6.672e-11 N m^2 / kg^2 (Sec. 2.1, below Eq. 2).
  * Units: density kg/m^3, gz in m/s^2, gradients in 1/s^2.
  *
@@ -119,6 +124,16 @@ static void orc_pair(const orc_mesh* g, int p, int q, int l, int m, int n,
               n * g->dz, (n + 1) * g->dz, out);
 }
 
+/* Kernel value for station (p, q, t) at the centre of cell (p, q, t) and
+ * cell (l, m, n): the equal-dimension variant. */
+static void orc_pair3d(const orc_mesh* g, int p, int q, int t, int l, int m, int n,
+                       double out[ORC_NCOMP_MAX])
+{
+    const double x = (p + 0.5) * g->dx, y = (q + 0.5) * g->dy, z = (t + 0.5) * g->dz;
+    orc_prism(x, y, z, l * g->dx, (l + 1) * g->dx, m * g->dy, (m + 1) * g->dy,
+              n * g->dz, (n + 1) * g->dz, out);
+}
+
 typedef struct {
     const orc_mesh* g;
     const double* rho;     /* [nz][ny][nx] */
@@ -147,6 +162,31 @@ static void* orc_forward_worker(void* arg)
                     const double rho = jb->rho[((size_t)n * g->ny + m) * g->nx + l];
                     double k[ORC_NCOMP_MAX];
                     orc_pair(g, p, q, l, m, n, k);
+                    for (int c = 0; c < nc; ++c) acc[c] += k[list[c]] * rho;
+                }
+        for (int c = 0; c < nc; ++c) jb->out[(size_t)c * jb->n_idx + s] = acc[c];
+    }
+    return NULL;
+}
+
+/* The same sum for stations at cell centres (equal-dimension variant):
+ * station index i = p + nx q + nx ny t. */
+static void* orc_forward3d_worker(void* arg)
+{
+    orc_job* jb = (orc_job*)arg;
+    const orc_mesh* g = jb->g;
+    int list[ORC_NCOMP_MAX];
+    const int nc = orc_comp_list(g->comps, list);
+    for (int s = jb->tid; s < jb->n_idx; s += jb->nthreads) {
+        const int st = jb->idx[s];
+        const int p = st % g->nx, q = (st / g->nx) % g->ny, t = st / (g->nx * g->ny);
+        double acc[ORC_NCOMP_MAX] = {0};
+        for (int n = 0; n < g->nz; ++n)
+            for (int m = 0; m < g->ny; ++m)
+                for (int l = 0; l < g->nx; ++l) {
+                    const double rho = jb->rho[((size_t)n * g->ny + m) * g->nx + l];
+                    double k[ORC_NCOMP_MAX];
+                    orc_pair3d(g, p, q, t, l, m, n, k);
                     for (int c = 0; c < nc; ++c) acc[c] += k[list[c]] * rho;
                 }
         for (int c = 0; c < nc; ++c) jb->out[(size_t)c * jb->n_idx + s] = acc[c];
@@ -259,6 +299,43 @@ int orc_gmatrix(int nx, int ny, int nz, double dx, double dy, double dz, double 
             orc_pair(&g, (int)(i % nx), (int)(i / nx), (int)(j % nx),
                      (int)((j / nx) % ny), (int)(j / nd), k);
             for (int c = 0; c < nc; ++c) G[((size_t)c * nd + i) * nm + j] = k[list[c]];
+        }
+    return 0;
+}
+
+/* Equal-dimension variant: forward at a subset of the stations at cell
+ * centres.  rho: [nz][ny][nx]; st_idx: station indices p + nx q + nx ny t;
+ * out: [ncomp][n_st].  h is not used.  Returns 0, or -1 on bad input. */
+int orc_forward3d(int nx, int ny, int nz, double dx, double dy, double dz,
+                  unsigned comps, const double* rho, int n_st, const int* st_idx,
+                  double* out, int nthreads)
+{
+    if (orc_check(nx, ny, nz, dx, dy, dz, 1.0, comps) || n_st < 0) return -1;
+    for (int s = 0; s < n_st; ++s)
+        if (st_idx[s] < 0 || st_idx[s] >= nx * ny * nz) return -1;
+    orc_mesh g = {nx, ny, nz, dx, dy, dz, 0.0, comps};
+    orc_job jb;
+    memset(&jb, 0, sizeof jb);
+    jb.g = &g; jb.rho = rho; jb.idx = st_idx; jb.n_idx = n_st; jb.out = out;
+    return orc_run(orc_forward3d_worker, &jb, nthreads);
+}
+
+/* Equal-dimension variant, explicit G for tiny meshes: G[c][i][j],
+ * i = p + nx q + nx ny t (station at the centre of cell i), j as above. */
+int orc_gmatrix3d(int nx, int ny, int nz, double dx, double dy, double dz,
+                  unsigned comps, double* G)
+{
+    if (orc_check(nx, ny, nz, dx, dy, dz, 1.0, comps)) return -1;
+    orc_mesh g = {nx, ny, nz, dx, dy, dz, 0.0, comps};
+    int list[ORC_NCOMP_MAX];
+    const int nc = orc_comp_list(comps, list);
+    const size_t nd = (size_t)nx * ny, nm = nd * nz;
+    for (size_t i = 0; i < nm; ++i)
+        for (size_t j = 0; j < nm; ++j) {
+            double k[ORC_NCOMP_MAX];
+            orc_pair3d(&g, (int)(i % nx), (int)((i / nx) % ny), (int)(i / nd), (int)(j % nx),
+                       (int)((j / nx) % ny), (int)(j / nd), k);
+            for (int c = 0; c < nc; ++c) G[((size_t)c * nm + i) * nm + j] = k[list[c]];
         }
     return 0;
 }

@@ -1,0 +1,104 @@
+"""Pins of the oracle's equal-dimension variant (Sec. 2.2, Eqs. 10-11: a
+station at the centre of every cell, data as three-dimensional as the mesh)
+against things other than itself: the block-Toeplitz structure in all three
+offsets, reduction to the already pinned observation-plane oracle for the
+cells below a station and, mirrored, for the cells above it, Poisson's
+equation inside a uniform mesh, and the exact field at a cube's centre."""
+import numpy as np
+import pytest
+
+import oracle
+
+ALL9 = 0x1FF
+UPS = 6.672e-11
+Z_ODD = [0, 3, 5]  # gz, gxz, gyz change sign under z -> -z; the others do not
+
+
+@pytest.fixture(scope="module", autouse=True)
+def built():
+    oracle.build()
+
+
+def test_forward_equals_explicit_G():
+    mesh = (4, 3, 3, 10.0, 12.0, 8.0, 1.0)
+    rho = np.random.default_rng(1).uniform(-300, 300, (3, 3, 4))
+    G = oracle.gmatrix3d(mesh, ALL9)
+    d = oracle.forward3d(mesh, ALL9, rho)
+    assert np.allclose(d.reshape(9, -1), np.einsum("cij,j->ci", G, rho.reshape(-1)), rtol=1e-13, atol=0)
+
+
+def test_three_level_toeplitz():
+    """G depends only on the offsets (l - p, m - q, n - t) (Eq. 10 in all
+    three axes): (2nx - 1)(2ny - 1)(2nz - 1) values per component, the count
+    of Eq. 11 without the virtual grid's extra row."""
+    nx, ny, nz = 4, 3, 3
+    mesh = (nx, ny, nz, 10.0, 12.0, 8.0, 1.0)
+    G = oracle.gmatrix3d(mesh, ALL9)
+    idx = np.arange(nx * ny * nz)
+    p, q, t = idx % nx, (idx // nx) % ny, idx // (nx * ny)
+    off = {}
+    for i in idx:
+        for j in idx:
+            key = (p[j] - p[i], q[j] - q[i], t[j] - t[i])
+            off.setdefault(key, []).append((i, j))
+    assert len(off) == (2 * nx - 1) * (2 * ny - 1) * (2 * nz - 1)
+    scale = np.abs(G).max(axis=(1, 2))
+    for pairs in off.values():
+        vals = np.array([G[:, i, j] for i, j in pairs])
+        assert np.all(np.abs(vals - vals[0]) <= 1e-12 * scale)
+
+
+@pytest.mark.parametrize("t", [0, 2])
+def test_cells_below_the_station_reduce_to_the_plane_oracle(t):
+    """With density only in the layers below station layer t, the field at
+    (p, q, t) is the observation-plane forward of those layers with the
+    stations dz / 2 above their top."""
+    nx, ny, nz, dx, dy, dz = 5, 4, 5, 10.0, 12.0, 8.0
+    rho = np.random.default_rng(2 + t).uniform(-300, 300, (nz, ny, nx))
+    rho[: t + 1] = 0.0
+    d3 = oracle.forward3d((nx, ny, nz, dx, dy, dz, 1.0), ALL9, rho)[:, t]
+    d2 = oracle.forward((nx, ny, nz - t - 1, dx, dy, dz, dz / 2), ALL9, rho[t + 1:])
+    assert np.allclose(d3, d2, rtol=1e-12, atol=1e-12 * np.abs(d2).max())
+
+
+@pytest.mark.parametrize("t", [2, 4])
+def test_cells_above_the_station_are_the_mirrored_plane_oracle(t):
+    """Density only above station layer t: reflecting z about the station's
+    depth maps those layers onto a mesh below a plane dz / 2 above it, so the
+    field is the plane forward of the reversed layers with the components
+    odd in z negated."""
+    nx, ny, nz, dx, dy, dz = 5, 4, 5, 10.0, 12.0, 8.0
+    rho = np.random.default_rng(7 + t).uniform(-300, 300, (nz, ny, nx))
+    rho[t:] = 0.0
+    d3 = oracle.forward3d((nx, ny, nz, dx, dy, dz, 1.0), ALL9, rho)[:, t]
+    d2 = oracle.forward((nx, ny, t, dx, dy, dz, dz / 2), ALL9, rho[:t][::-1])
+    d2[Z_ODD] *= -1.0
+    assert np.allclose(d3, d2, rtol=1e-12, atol=1e-12 * np.abs(d2).max())
+
+
+def test_uniform_mesh_obeys_poisson():
+    """A uniform density rho0 everywhere: every station is inside the body,
+    so the trace of the gradient tensor is -4 pi upsilon rho0 at each."""
+    mesh = (5, 4, 3, 10.0, 12.0, 8.0, 1.0)
+    rho0 = 250.0
+    d = oracle.forward3d(mesh, 0x52, np.full((3, 4, 5), rho0))  # gxx, gyy, gzz
+    trace = d.sum(axis=0)
+    assert np.allclose(trace, -4 * np.pi * UPS * rho0, rtol=1e-12, atol=0)
+
+
+def test_own_cell_of_a_cube_mesh():
+    """Only the station's own cell (a cube) carries density: the odd
+    components vanish there and each diagonal one is -4 pi upsilon rho / 3."""
+    nx, ny, nz = 3, 3, 3
+    rho = np.zeros((nz, ny, nx))
+    rho[1, 1, 1] = 300.0
+    d = oracle.forward3d((nx, ny, nz, 10.0, 10.0, 10.0, 1.0), ALL9, rho)[:, 1, 1, 1]
+    assert np.allclose(d[[0, 2, 3, 5, 7, 8]], 0.0, atol=1e-14 * 4 * np.pi * UPS * 300.0)
+    assert np.allclose(d[[1, 4, 6]], -4 * np.pi * UPS * 300.0 / 3, rtol=1e-13)
+
+
+def test_invalid_arguments():
+    with pytest.raises(ValueError):
+        oracle.forward3d((0, 2, 2, 1.0, 1.0, 1.0, 1.0), 1, np.zeros(0))
+    with pytest.raises(ValueError):
+        oracle.forward3d((2, 2, 2, 1.0, 1.0, 1.0, 1.0), 1, np.zeros((2, 2, 2)), stations=[8])
