@@ -102,3 +102,68 @@ def test_invalid_arguments():
         oracle.forward3d((0, 2, 2, 1.0, 1.0, 1.0, 1.0), 1, np.zeros(0))
     with pytest.raises(ValueError):
         oracle.forward3d((2, 2, 2, 1.0, 1.0, 1.0, 1.0), 1, np.zeros((2, 2, 2)), stations=[8])
+
+
+# Planted mistakes in the equal-dimension code of the oracle's C source; each
+# must fail the reduction pins above (built and run the same way as
+# tests/test_oracle_mutants.py does for the plane oracle).
+MUTANTS_3D = {
+    "station_depth_at_cell_bottom": ("z = (t + 0.5) * g->dz", "z = (t + 1.0) * g->dz"),
+    "station_layer_index": ("t = st / (g->nx * g->ny)", "t = st / g->nx % g->nz"),
+    "station_y_uses_dx": ("y = (q + 0.5) * g->dy, z = (t + 0.5)", "y = (q + 0.5) * g->dx, z = (t + 0.5)"),
+}
+
+
+def _build_lib(tmp_path, name, old, new):
+    import ctypes
+    import os
+    import subprocess
+
+    src = open(os.path.join(os.path.dirname(oracle.__file__), "prism_oracle.c")).read()
+    assert src.count(old) == 1, name
+    c_path, so_path = tmp_path / f"{name}.c", tmp_path / f"{name}.so"
+    c_path.write_text(src.replace(old, new))
+    subprocess.run(["gcc", "-O2", "-std=c11", "-fPIC", "-shared", "-o", str(so_path), str(c_path), "-lm",
+                    "-lpthread"], check=True)
+    lib = ctypes.CDLL(str(so_path))
+    d, i, u, p = ctypes.c_double, ctypes.c_int, ctypes.c_uint, ctypes.c_void_p
+    lib.orc_forward.argtypes = [i, i, i, d, d, d, d, u, p, i, p, p, i]
+    lib.orc_forward3d.argtypes = [i, i, i, d, d, d, u, p, i, p, p, i]
+    return lib
+
+
+def _reductions_hold(lib):
+    """The below- and above-the-station reductions of the pins, run on lib."""
+    import ctypes
+
+    nx, ny, nz, dx, dy, dz = 4, 3, 5, 10.0, 12.0, 8.0
+    ptr = lambda a: a.ctypes.data_as(ctypes.c_void_p)  # noqa: E731
+    for t, below in ((1, True), (3, False)):
+        rho = np.random.default_rng(t).uniform(-300, 300, (nz, ny, nx))
+        if below:
+            rho[: t + 1] = 0.0
+            sub = np.ascontiguousarray(rho[t + 1:])
+        else:
+            rho[t:] = 0.0
+            sub = np.ascontiguousarray(rho[:t][::-1])
+        st3 = (np.arange(nx * ny) + t * nx * ny).astype(np.int32)
+        d3 = np.zeros((9, nx * ny))
+        lib.orc_forward3d(nx, ny, nz, dx, dy, dz, ALL9, ptr(rho), nx * ny, ptr(st3), ptr(d3), 1)
+        st2 = np.arange(nx * ny, dtype=np.int32)
+        d2 = np.zeros((9, nx * ny))
+        lib.orc_forward(nx, ny, sub.shape[0], dx, dy, dz, dz / 2, ALL9, ptr(sub), nx * ny, ptr(st2), ptr(d2), 1)
+        if not below:
+            d2[Z_ODD] *= -1.0
+        if not np.allclose(d3, d2, rtol=1e-10, atol=1e-10 * np.abs(d2).max()):
+            return False
+    return True
+
+
+def test_unmutated_equal_dim_code_passes(tmp_path):
+    assert _reductions_hold(_build_lib(tmp_path, "original", "#include <math.h>", "#include <math.h>"))
+
+
+@pytest.mark.parametrize("name", sorted(MUTANTS_3D))
+def test_equal_dim_mutant_is_caught(tmp_path, name):
+    old, new = MUTANTS_3D[name]
+    assert not _reductions_hold(_build_lib(tmp_path, name, old, new)), f"planted mistake {name} was not caught"
