@@ -97,6 +97,35 @@ def test_own_cell_of_a_cube_mesh():
     assert np.allclose(d[[1, 4, 6]], -4 * np.pi * UPS * 300.0 / 3, rtol=1e-13)
 
 
+def test_three_level_circulant_spectra_are_real_or_imaginary():
+    """The structure a transform-based equal-dimension path relies on, from
+    the oracle's explicit G: embedded in a three-level circulant (negative
+    offsets wrapped), each component's kernel has a purely real or purely
+    imaginary spectrum (gz, gx, gy imaginary; gxx, gxy, gxz, gyy, gyz, gzz
+    real: odd in an odd number of axes), and the circulant product equals
+    the direct sum."""
+    nx, ny, nz = 5, 4, 3
+    mesh = (nx, ny, nz, 10.0, 12.0, 8.0, 1.0)
+    G = oracle.gmatrix3d(mesh, ALL9)
+    rho = np.random.default_rng(4).normal(size=(nz, ny, nx))
+    ref = oracle.forward3d(mesh, ALL9, rho)
+    Px, Py, Pz = 16, 8, 8  # powers of two >= 2n - 1 (9, 7, 5)
+    i = np.arange(nx * ny * nz)
+    p, q, t = i % nx, (i // nx) % ny, i // (nx * ny)
+    R = np.zeros((Pz, Py, Px))
+    R[:nz, :ny, :nx] = rho
+    imaginary = {0, 7, 8}
+    for c in range(9):
+        K = np.zeros((Pz, Py, Px))
+        # d(i) = sum_j K(j - i) rho(j): K(-offset) stored at offset mod P (a circular convolution)
+        K[(t[:, None] - t[None, :]) % Pz, (q[:, None] - q[None, :]) % Py, (p[:, None] - p[None, :]) % Px] = G[c]
+        S = np.fft.fftn(K)
+        small = (np.abs(S.real) if c in imaginary else np.abs(S.imag)).max()
+        assert small <= 1e-12 * np.abs(S).max(), c
+        d = np.real(np.fft.ifftn(S * np.fft.fftn(R)))[:nz, :ny, :nx]
+        assert np.abs(d - ref[c]).max() <= 1e-12 * np.abs(ref[c]).max(), c
+
+
 def test_invalid_arguments():
     with pytest.raises(ValueError):
         oracle.forward3d((0, 2, 2, 1.0, 1.0, 1.0, 1.0), 1, np.zeros(0))
