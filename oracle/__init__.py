@@ -78,6 +78,8 @@ def _load():
             lib.orc_gmatrix.restype = i
             lib.orc_forward3d.argtypes = [i, i, i, d, d, d, u, p, i, p, p, i]
             lib.orc_forward3d.restype = i
+            lib.orc_adjoint3d.argtypes = [i, i, i, d, d, d, u, p, i, p, p, i]
+            lib.orc_adjoint3d.restype = i
             lib.orc_gmatrix3d.argtypes = [i, i, i, d, d, d, u, p]
             lib.orc_gmatrix3d.restype = i
             _lib = lib
@@ -209,6 +211,25 @@ def forward3d(mesh, comps: int, rho: np.ndarray, stations=None, nthreads=None) -
     if rc != 0:
         raise ValueError("orc_forward3d: invalid arguments")
     return out.reshape(nc, nz, ny, nx) if full else out
+
+
+def adjoint3d(mesh, comps: int, resid: np.ndarray, cells=None, nthreads=None) -> np.ndarray:
+    """Equal-dimension variant: (G^T r)_j = sum_c sum_i G_c(i, j) r_c(i) over
+    the stations at cell centres.  resid is [ncomp][nz][ny][nx]; ``cells`` an
+    optional list of cell indices.  Returns [nz][ny][nx] or [n_cells]."""
+    lib = _load()
+    nx, ny, nz, dx, dy, dz, _ = _geom(mesh)
+    nc = len(comp_list(comps))
+    resid = np.ascontiguousarray(resid, dtype=np.float64).reshape(nc, nz, ny, nx)
+    full = cells is None
+    idx = np.arange(nx * ny * nz, dtype=np.int32) if full else np.ascontiguousarray(cells, dtype=np.int32)
+    out = np.zeros(idx.size, dtype=np.float64)
+    rc = lib.orc_adjoint3d(nx, ny, nz, dx, dy, dz, comps, resid.ctypes.data_as(ctypes.c_void_p), int(idx.size),
+                           idx.ctypes.data_as(ctypes.c_void_p), out.ctypes.data_as(ctypes.c_void_p),
+                           int(nthreads or default_threads()))
+    if rc != 0:
+        raise ValueError("orc_adjoint3d: invalid arguments")
+    return out.reshape(nz, ny, nx) if full else out
 
 
 def gmatrix3d(mesh, comps: int) -> np.ndarray:

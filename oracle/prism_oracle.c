@@ -219,6 +219,32 @@ static void* orc_adjoint_worker(void* arg)
     return NULL;
 }
 
+/* Equal-dimension variant: (G^T r)(cell) over the stations at cell centres;
+ * r: [ncomp][nz][ny][nx]. */
+static void* orc_adjoint3d_worker(void* arg)
+{
+    orc_job* jb = (orc_job*)arg;
+    const orc_mesh* g = jb->g;
+    int list[ORC_NCOMP_MAX];
+    const int nc = orc_comp_list(g->comps, list);
+    const size_t nm = (size_t)g->nx * g->ny * g->nz;
+    for (int s = jb->tid; s < jb->n_idx; s += jb->nthreads) {
+        const int cell = jb->idx[s];
+        const int l = cell % g->nx, m = (cell / g->nx) % g->ny, n = cell / (g->nx * g->ny);
+        double acc = 0.0;
+        for (int t = 0; t < g->nz; ++t)
+            for (int q = 0; q < g->ny; ++q)
+                for (int p = 0; p < g->nx; ++p) {
+                    double k[ORC_NCOMP_MAX];
+                    orc_pair3d(g, p, q, t, l, m, n, k);
+                    const size_t i = ((size_t)t * g->ny + q) * g->nx + p;
+                    for (int c = 0; c < nc; ++c) acc += k[list[c]] * jb->resid[(size_t)c * nm + i];
+                }
+        jb->out[s] = acc;
+    }
+    return NULL;
+}
+
 static int orc_run(void* (*fn)(void*), orc_job* proto, int nthreads)
 {
     if (nthreads < 1) nthreads = 1;
@@ -318,6 +344,23 @@ int orc_forward3d(int nx, int ny, int nz, double dx, double dy, double dz,
     memset(&jb, 0, sizeof jb);
     jb.g = &g; jb.rho = rho; jb.idx = st_idx; jb.n_idx = n_st; jb.out = out;
     return orc_run(orc_forward3d_worker, &jb, nthreads);
+}
+
+/* Equal-dimension variant: adjoint at a subset of cells.  resid:
+ * [ncomp][nz][ny][nx] (one value per station at a cell centre); cell_idx:
+ * cell indices l + nx m + nx ny n; out: [n_cells]. */
+int orc_adjoint3d(int nx, int ny, int nz, double dx, double dy, double dz,
+                  unsigned comps, const double* resid, int n_cells, const int* cell_idx,
+                  double* out, int nthreads)
+{
+    if (orc_check(nx, ny, nz, dx, dy, dz, 1.0, comps) || n_cells < 0) return -1;
+    for (int s = 0; s < n_cells; ++s)
+        if (cell_idx[s] < 0 || cell_idx[s] >= nx * ny * nz) return -1;
+    orc_mesh g = {nx, ny, nz, dx, dy, dz, 0.0, comps};
+    orc_job jb;
+    memset(&jb, 0, sizeof jb);
+    jb.g = &g; jb.resid = resid; jb.idx = cell_idx; jb.n_idx = n_cells; jb.out = out;
+    return orc_run(orc_adjoint3d_worker, &jb, nthreads);
 }
 
 /* Equal-dimension variant, explicit G for tiny meshes: G[c][i][j],

@@ -27,6 +27,24 @@ def test_forward_equals_explicit_G():
     assert np.allclose(d.reshape(9, -1), np.einsum("cij,j->ci", G, rho.reshape(-1)), rtol=1e-13, atol=0)
 
 
+def test_adjoint_is_the_transpose():
+    """adjoint3d equals the explicit G transposed, and <G x, r> = <x, G^T r>
+    holds on a larger mesh without the explicit G."""
+    mesh = (4, 3, 3, 10.0, 12.0, 8.0, 1.0)
+    rng = np.random.default_rng(6)
+    r = rng.normal(size=(9, 3, 3, 4))
+    G = oracle.gmatrix3d(mesh, ALL9)
+    got = oracle.adjoint3d(mesh, ALL9, r).reshape(-1)
+    want = np.einsum("cij,ci->j", G, r.reshape(9, -1))
+    assert np.allclose(got, want, rtol=1e-13, atol=1e-13 * np.abs(want).max())
+    mesh = (7, 6, 5, 10.0, 12.0, 8.0, 1.0)
+    x = rng.normal(size=(5, 6, 7))
+    r = rng.normal(size=(9, 5, 6, 7))
+    lhs = float((oracle.forward3d(mesh, ALL9, x) * r).sum())
+    rhs = float((x * oracle.adjoint3d(mesh, ALL9, r)).sum())
+    assert abs(lhs - rhs) <= 1e-12 * max(abs(lhs), abs(rhs))
+
+
 def test_three_level_toeplitz():
     """G depends only on the offsets (l - p, m - q, n - t) (Eq. 10 in all
     three axes): (2nx - 1)(2ny - 1)(2nz - 1) values per component, the count
