@@ -63,6 +63,8 @@ def parse():
     ap.add_argument("--serve-requests", type=int, default=10000,
                     help="requests in the serving leg (Poisson arrivals, 0 to skip)")
     ap.add_argument("--serve-rate", type=float, default=200.0, help="mean arrival rate of the serving leg (1/s)")
+    ap.add_argument("--equal-dim", default="1024,1024,100",
+                    help="nx,ny,nz of the equal-dimension leg (grf1024 geometry; 'none' to skip)")
     return ap.parse_args()
 
 
@@ -298,6 +300,59 @@ def serving_leg(n_requests: int, rate: float):
     return st
 
 
+def equal_dim_leg(dims: str, dev, peak: float):
+    """Forward and adjoint of the equal-dimension variant (a station at the
+    centre of every cell) on the grf1024 geometry (50 x 50 x 25 m cells) with
+    the smooth random-field density, six components, FP32 spectra; device
+    time by CUDA events.  Method bytes: the stored three-level spectra + rho +
+    the six output volumes."""
+    import torch
+
+    from paper_2005_10160_gb300 import workloads
+    from paper_2005_10160_gb300.plan import Plan3D
+
+    nx, ny, nz = (int(v) for v in dims.split(","))
+    mesh, rho = workloads.grf1024(nx, ny, nz, device=dev)
+    rho = rho.contiguous()
+    t0 = time.perf_counter()
+    plan = Plan3D(mesh, COMPS, fp64=False)
+    torch.cuda.synchronize()
+    plan_s = time.perf_counter() - t0
+    out = torch.empty((NCOMP, nz, ny, nx), dtype=torch.float32, device=dev)
+    grad = torch.empty((nz, ny, nx), dtype=torch.float32, device=dev)
+    stream = torch.cuda.current_stream(dev)
+    for _ in range(2):
+        plan.forward(rho, out)
+        plan.adjoint(out, grad)
+    torch.cuda.synchronize()
+    n = 5
+    e0, e1, e2 = (torch.cuda.Event(enable_timing=True) for _ in range(3))
+    e0.record(stream)
+    for _ in range(n):
+        plan.forward(rho, out)
+    e1.record(stream)
+    for _ in range(n):
+        plan.adjoint(out, grad)
+    e2.record(stream)
+    torch.cuda.synchronize()
+    f_ms = e0.elapsed_time(e1) / n
+    a_ms = e1.elapsed_time(e2) / n
+    cells = float(nx * ny * nz)
+    pairs = cells * cells
+    method = plan.spectra_bytes + 4 * cells + 4 * NCOMP * cells
+    res = {"workload": f"equal-dimension {nx}x{ny}x{nz} cells 50x50x25 m, a station at every cell centre, "
+                       f"{NCOMP} components, FP32 spectra, smooth random-field density",
+           "pairs_per_forward": pairs, "plan_create_s": plan_s, "pz": plan.pz,
+           "forward_ms": f_ms, "forward_pairs_per_s": pairs / (f_ms / 1000.0),
+           "adjoint_ms": a_ms, "adjoint_pairs_per_s": pairs / (a_ms / 1000.0),
+           "method_bytes": method, "spectra_bytes": plan.spectra_bytes,
+           "forward_frac": method / (f_ms / 1000.0) / 1e9 / peak,
+           "adjoint_frac": method / (a_ms / 1000.0) / 1e9 / peak,
+           "frac_what": "(stored spectra + rho + out) / device time / measured HBM copy bandwidth"}
+    plan.close()
+    return res
+
+
 def run_reference(args):
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -402,23 +457,30 @@ def run_ours(args):
     ms_per_step = ms_max / args.steps
     value = whole_job_rate(world, pairs, args.steps, ms_max)
 
-    # roofline of the dominant kernel: the column stage
+    # roofline of the dominant kernel, the column stage, on the method's own
+    # bytes: the stored kernel spectra it streams once (one FP32 real per
+    # (kx, mirror pair, layer, component); they replace G, Eq. 22)
     kx = plan.px // 2 + 1
     hy = plan.py // 2 + 1
     spec_b = NCOMP * nz * kx * hy * 4
-    x_b = kx * nz * ny * 8
-    y_b = 2 * kx * NCOMP * ny * 8
-    col_alg = spec_b + x_b + y_b
+    x_b = kx * nz * ny * 8          # row transforms of rho, read (implementation traffic)
+    y_b = 2 * kx * NCOMP * ny * 8   # column outputs, written (implementation traffic)
     col_ms = stage_ms["forward_columns"] / max(1, n_fwd)
     peak, peak_kind = hbm_peak()
-    achieved = col_alg / (col_ms / 1000.0) / 1e9
+    achieved = spec_b / (col_ms / 1000.0) / 1e9
     digest = kernel_digest()
     traffic = profiled_traffic(digest)
+    fwd_alg = spec_b + 4 * nx * ny * nz + 4 * NCOMP * nx * ny  # spectra + rho + out
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
                 "traffic": traffic, "kernel": "forward_column_wf_kernel<6> (column stage)",
-                "algorithmic_bytes": col_alg, "avg_launch_ms": col_ms, "peak_kind": peak_kind,
+                "algorithmic_bytes": spec_b, "avg_launch_ms": col_ms, "peak_kind": peak_kind,
+                "dram_efficiency": {"bytes": spec_b + x_b + y_b,
+                                    "frac": (spec_b + x_b + y_b) / (col_ms / 1000.0) / 1e9 / peak,
+                                    "what": "spectra + row transforms read + column outputs written, per launch"},
+                "whole_forward": {"bytes": fwd_alg, "ms": ms_per_step,
+                                  "frac": fwd_alg / (ms_per_step / 1000.0) / 1e9 / peak,
+                                  "what": "stored spectra + rho + out over the device time of one forward"},
                 "stage_ms": {k: v / max(1, n_fwd) for k, v in stage_ms.items() if k.startswith("forward")}}
-    fwd_alg = spec_b + 4 * nx * ny * nz + 4 * NCOMP * nx * ny
 
     # end to end through the public API with pinned host buffers
     rho_h = rho.cpu().pin_memory()
@@ -490,8 +552,12 @@ def run_ours(args):
     a_stage, _, n_adj = capi.grav_plan_stage_times(plan.handle)
     capi.grav_plan_set_timing(plan.handle, False)
     a_ms = max_over_ranks(world, a0.elapsed_time(a1)) / a_steps
+    a_col_ms = a_stage["adjoint_columns"] / max(1, n_adj)
+    adj_alg = spec_b + 4 * NCOMP * nx * ny + 4 * nx * ny * nz  # spectra + r + grad
     adjoint = {"ms_per_step": a_ms, "value": whole_job_rate(world, pairs, 1, a_ms), "unit": "pairs/s", "steps": a_steps,
-               "stage_ms": {k: v / max(1, n_adj) for k, v in a_stage.items() if k.startswith("adjoint")}}
+               "stage_ms": {k: v / max(1, n_adj) for k, v in a_stage.items() if k.startswith("adjoint")},
+               "column_stage_frac": spec_b / (a_col_ms / 1000.0) / 1e9 / peak,
+               "whole_adjoint_frac": adj_alg / (a_ms / 1000.0) / 1e9 / peak}
     del r_in, grad
 
     # the all-FP64 spectral path on the same workload, for context
@@ -510,10 +576,16 @@ def run_ours(args):
         f1.record(stream)
         torch.cuda.synchronize()
         ms64 = f0.elapsed_time(f1) / n64
-        rel = (torch.linalg.vector_norm((out.double() - out64).reshape(NCOMP, -1), dim=1)
+        diff = (out.double() - out64).reshape(NCOMP, -1)
+        rel = (torch.linalg.vector_norm(diff, dim=1)
                / torch.linalg.vector_norm(out64.reshape(NCOMP, -1), dim=1)).cpu().tolist()
+        units = torch.tensor([1e5] + [1e9] * (NCOMP - 1), dtype=torch.float64, device=dev)  # mGal, Eotvos
+        maxabs = (diff.abs().amax(dim=1) * units).cpu().tolist()
+        peak_val = (out64.reshape(NCOMP, -1).abs().amax(dim=1) * units).cpu().tolist()
         fp64 = {"ms_per_step": ms64, "value": pairs / (ms64 / 1000.0),
-                "fp32_vs_fp64_rel_l2": rel}
+                "fp32_vs_fp64_rel_l2": rel, "fp32_vs_fp64_max_abs_mgal_eotvos": maxabs,
+                "field_max_abs_mgal_eotvos": peak_val,
+                "components": ["gz (mGal)", "gxx (E)", "gxy (E)", "gxz (E)", "gyy (E)", "gyz (E)"]}
         plan64.close()
         del rho64, out64
 
@@ -537,6 +609,12 @@ def run_ours(args):
                                  "depth weights beta = 2, damped CGLS",
                      "iterations": res.iterations, "ms_per_iteration": res.ms_per_iteration,
                      "lam": res.lam, "objective_first": res.objectives[0], "objective_last": res.objectives[-1]}
+
+    # the equal-dimension variant (a station at every cell centre, Eqs. 10-11)
+    equal_dim = None
+    if rank == 0 and args.equal_dim != "none":
+        plan.close()
+        equal_dim = equal_dim_leg(args.equal_dim, dev, peak)
 
     serving = None
     if rank == 0 and args.serve_requests > 0:
@@ -564,6 +642,7 @@ def run_ours(args):
                        "forward_algorithmic_bytes": fwd_alg},
             "roofline": roofline, "clocks": clocks, "e2e": e2e, "gpu_launches": 3 * args.steps,
             "cpu_baseline": cpu, "fp64_path": fp64, "adjoint": adjoint, "inversion": inversion, "serving": serving,
+            "equal_dim": equal_dim,
         }
         print(json.dumps(line), flush=True)
     plan.close()

@@ -77,10 +77,17 @@ enum {
     GRAV_EINVAL = -1,   /* bad size, spacing, height, mask or null pointer */
     GRAV_ENOMEM = -2,   /* device memory (HBM) exhausted */
     GRAV_ECUDA = -3,    /* a CUDA call failed; the message names it */
-    GRAV_ETIMEOUT = -4  /* reserved: a bounded device wait gave up */
+    GRAV_ETIMEOUT = -4  /* a bounded device wait gave up (grav_plan_check) */
 };
 
-/* Limits of this implementation. */
+/* Limits of this implementation.  They differ per axis on purpose: the row
+ * stage (x) streams rows of up to 4096 points through registers, while the
+ * column stage (y) keeps a whole half-length column transform of every layer
+ * in one CTA's shared memory, which caps Py at 2048 (ny <= 1024).  A mesh
+ * with ny > 1024 and nx <= 1024 is computed with the axes exchanged:
+ * transpose rho's x and y, swap dx and dy, and read gxx as gyy, gxz as gyz,
+ * gx as gy (and back); gz, gxy and gzz are unchanged.  A 2048 x 2048 mesh is
+ * beyond this version. */
 #define GRAV_MAX_NX 2048
 #define GRAV_MAX_NY 1024
 
@@ -156,6 +163,8 @@ typedef struct {
     int fp64;                /* 1 with GRAV_FP64_SPECTRAL */
     size_t spectra_bytes;    /* resident kernel spectra */
     size_t workspace_bytes;  /* per-call scratch owned by the plan */
+    int pz;                  /* circulant size along z (equal-dimension plans), else 0 */
+    int equal_dim;           /* 1 for a plan made by grav_plan_create3d */
 } grav_plan_info_t;
 
 /* Fill *info.  Returns GRAV_OK or GRAV_EINVAL. */
@@ -201,6 +210,44 @@ int grav_plan_check(grav_plan* plan);
  * stays usable.  GRAV_OK would mean the wait did not run out. */
 int grav_selftest_bounded_wait(double limit_ms, double* waited_ms);
 
+/* ---- Equal-dimension variant (Sec. 2.2, Eqs. 10-11) ----
+ *
+ * A station at the centre of every cell: station (p, q, t) sits at
+ * ((p + 1/2) dx, (q + 1/2) dy, (t + 1/2) dz), inside the mesh, and the data are
+ * as three-dimensional as the model (the case the paper sizes at 1024 x 1024 x
+ * 100 cells).  G(station (p,q,t), cell (l,m,n)) depends only on the offset
+ * (l-p, m-q, n-t), so G is block Toeplitz on all three levels (the block
+ * matrix of G_{t,n} after Eq. 22) with (2nx-1)(2ny-1)(2nz-1) distinct values.
+ * The plan embeds them in a three-level circulant (Eq. 19 on every axis) and
+ * keeps its spectra; a forward is a three-dimensional FFT product.  At a
+ * station's own cell the closed forms give the field inside the prism.
+ *
+ * Layouts: rho and grad [nz][ny][nx]; out and r [ncomp][nz][ny][nx] (one
+ * value per station and component, components in ascending bit order).
+ * Precision flag, units, streams, ownership and errors as for the plane
+ * plans.  Limits: nx, ny <= 1024, nz <= 512, at most 8 components. */
+
+/* Build an equal-dimension plan (kernel over the offsets of Eq. 10 with
+ * the layer offset as a third index, Eq. 11; three-level circulant spectra).
+ * Blocks until done.  Arguments as grav_plan_create without h.  Returns NULL
+ * on error (see grav_last_error).  Release it with grav_plan_destroy;
+ * grav_plan_bytes and grav_plan_info apply; grav_forward, grav_adjoint and
+ * the batched and static-scratch calls reject it with GRAV_EINVAL. */
+grav_plan* grav_plan_create3d(int nx, int ny, int nz, double dx, double dy, double dz, unsigned components);
+
+/* d_c(p,q,t) = sum_{l,m,n} K_c(l-p, m-q, n-t) rho(l,m,n) at every cell centre.
+ *   rho_dev  device [nz][ny][nx]
+ *   out_dev  device [ncomp][nz][ny][nx]; fully overwritten
+ * Returns GRAV_OK, GRAV_EINVAL (null pointer, or not an equal-dimension
+ * plan) or GRAV_ECUDA. */
+int grav_forward3d(grav_plan* plan, const void* rho_dev, void* out_dev, void* stream);
+
+/* Transpose: grad(l,m,n) = sum_c sum_{p,q,t} K_c(l-p, m-q, n-t) r_c(p,q,t).
+ *   r_dev     device [ncomp][nz][ny][nx]
+ *   grad_dev  device [nz][ny][nx]; fully overwritten
+ * Status codes as grav_forward3d. */
+int grav_adjoint3d(grav_plan* plan, const void* r_dev, void* grad_dev, void* stream);
+
 /* Size of the library's static device scratch area (16 MiB per GPU). */
 #define GRAV_STATIC_SCRATCH_BYTES (16u << 20)
 
@@ -225,6 +272,8 @@ int grav_selftest_bounded_wait(double limit_ms, double* waited_ms);
  *   - the current device must be the plan's device (GRAV_EINVAL otherwise).
  *   - the first call on a device looks up the array's device address with
  *     that device current; make that first call before any stream capture.
+ *     The address is looked up again whenever the device's CUDA context is
+ *     a new one (after cudaDeviceReset), on the first call made after that.
  *   - every call, on any plan, shares the one array: calls whose work
  *     overlaps on the GPU race and give wrong results.  Order them on one
  *     stream or with events.  No contents need clearing between calls. */

@@ -43,6 +43,9 @@ EXPORTED = (
     "grav_workspace_bytes",
     "grav_forward_batch",
     "grav_adjoint_batch",
+    "grav_plan_create3d",
+    "grav_forward3d",
+    "grav_adjoint3d",
 )
 
 
@@ -58,6 +61,7 @@ class grav_plan_info_t(ctypes.Structure):
         ("px", ctypes.c_int), ("py", ctypes.c_int),
         ("ncomp", ctypes.c_int), ("fp64", ctypes.c_int),
         ("spectra_bytes", ctypes.c_size_t), ("workspace_bytes", ctypes.c_size_t),
+        ("pz", ctypes.c_int), ("equal_dim", ctypes.c_int),
     ]
 
 
@@ -108,6 +112,12 @@ def lib() -> ctypes.CDLL:
             L.grav_forward_batch.restype = i
             L.grav_adjoint_batch.argtypes = [p, i, p, p, p, p]
             L.grav_adjoint_batch.restype = i
+            L.grav_plan_create3d.argtypes = [i, i, i, d, d, d, u]
+            L.grav_plan_create3d.restype = p
+            L.grav_forward3d.argtypes = [p, p, p, p]
+            L.grav_forward3d.restype = i
+            L.grav_adjoint3d.argtypes = [p, p, p, p]
+            L.grav_adjoint3d.restype = i
             _lib = L
     return _lib
 
@@ -209,3 +219,21 @@ def grav_forward_batch(plan, batch, rho_ptr, out_ptr, ws_ptr, stream=0) -> int:
 
 def grav_adjoint_batch(plan, batch, r_ptr, grad_ptr, ws_ptr, stream=0) -> int:
     return _check(lib().grav_adjoint_batch(plan, int(batch), r_ptr, grad_ptr, ws_ptr or None, stream or None))
+
+
+def grav_plan_create3d(nx, ny, nz, dx, dy, dz, components) -> int:
+    """Equal-dimension plan (a station at every cell centre); raises GravError on failure."""
+    ptr = lib().grav_plan_create3d(int(nx), int(ny), int(nz), float(dx), float(dy), float(dz), int(components))
+    if not ptr:
+        msg = grav_last_error()
+        code = GRAV_ENOMEM if ("memory" in msg or "cudaMalloc" in msg) else GRAV_EINVAL
+        raise GravError(code, msg)
+    return ptr
+
+
+def grav_forward3d(plan, rho_ptr, out_ptr, stream=0) -> int:
+    return _check(lib().grav_forward3d(plan, rho_ptr, out_ptr, stream or None))
+
+
+def grav_adjoint3d(plan, r_ptr, grad_ptr, stream=0) -> int:
+    return _check(lib().grav_adjoint3d(plan, r_ptr, grad_ptr, stream or None))

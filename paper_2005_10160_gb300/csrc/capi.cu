@@ -27,6 +27,7 @@ thread_local char g_err[512] = "";
 template <typename R> struct cplx_of;
 template <> struct cplx_of<float> { using type = float2; };
 template <> struct cplx_of<double> { using type = double2; };
+}  // namespace
 
 int ilog2(int v) {
     int l = 0;
@@ -44,6 +45,8 @@ int circulant_size(int n) {
 }
 
 size_t round_up(size_t v, size_t m) { return (v + m - 1) / m * m; }
+
+namespace {
 
 // exp(-2 pi i e / T) with exact quadrant symmetry; T is a power of two >= 4.
 void unit_root(long e, long T, double* re, double* im) {
@@ -70,6 +73,8 @@ void unit_root(long e, long T, double* re, double* im) {
     *re = ct;
     *im = -st;
 }
+
+}  // namespace
 
 int check_geometry(int nx, int ny, int nz, double dx, double dy, double dz, double h, unsigned components) {
     if (nx < 1 || ny < 1 || nz < 1 || nx > GRAV_MAX_NX || ny > GRAV_MAX_NY) {
@@ -100,6 +105,19 @@ int check_geometry(int nx, int ny, int nz, double dx, double dy, double dz, doub
     return GRAV_OK;
 }
 
+int dev_alloc_raw(void** p, size_t bytes, const char* what) {
+    cudaError_t e = cudaMalloc(p, bytes);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        *p = nullptr;
+        set_error("cudaMalloc of %zu bytes for %s failed: %s", bytes, what, cudaGetErrorString(e));
+        return e == cudaErrorMemoryAllocation ? GRAV_ENOMEM : GRAV_ECUDA;
+    }
+    return GRAV_OK;
+}
+
+namespace {
+
 template <typename T>
 int dev_alloc(T** p, size_t bytes, const char* what) {
     cudaError_t e = cudaMalloc((void**)p, bytes);
@@ -111,6 +129,8 @@ int dev_alloc(T** p, size_t bytes, const char* what) {
     }
     return GRAV_OK;
 }
+
+}  // namespace
 
 void free_plan(grav_plan* p) {
     if (!p) return;
@@ -153,6 +173,8 @@ int build_twiddles(int log_t, int fp64, void** dev, size_t* bytes) {
     free(host);
     return rc;
 }
+
+namespace {
 
 template <typename R>
 int make_spectra(grav_plan* p) {
@@ -321,6 +343,10 @@ int batch_call(grav_plan* plan, int batch, const void* in, void* out, void* ws, 
         set_error("%s: null plan or buffer, or batch outside 1..65535", name);
         return GRAV_EINVAL;
     }
+    if (plan->kind != 0) {
+        set_error("%s: the plan was made by grav_plan_create3d; use grav_forward3d / grav_adjoint3d", name);
+        return GRAV_EINVAL;
+    }
     if (!ws && batch > 1) {
         set_error("%s: a batch of %d needs a workspace of %d x grav_workspace_bytes", name, batch, batch);
         return GRAV_EINVAL;
@@ -478,6 +504,8 @@ int grav_plan_info(const grav_plan* plan, grav_plan_info_t* info) {
     info->fp64 = plan->fp64;
     info->spectra_bytes = plan->spec_bytes;
     info->workspace_bytes = plan->ws_a_bytes + plan->ws_b_bytes;
+    info->pz = plan->kind == 1 ? plan->pz : 0;
+    info->equal_dim = plan->kind == 1 ? 1 : 0;
     return GRAV_OK;
 }
 

@@ -60,6 +60,7 @@ struct ColumnArgs {
 }  // namespace grav
 
 struct grav_plan {
+    int kind;  // 0: stations on a plane above the mesh; 1: a station at every cell centre (grav_plan_create3d)
     int nx, ny, nz;
     double dx, dy, dz, h;
     unsigned comps;
@@ -79,6 +80,11 @@ struct grav_plan {
     size_t spec_bytes, tw_bytes, ws_a_bytes, ws_b_bytes;
     int* err_flag;  // device int: a pipeline wait ran out
     int device;
+    // equal-dimension plans (kind 1): circulant size along z and the z parity
+    // of each component slot; spec holds spec3[c][kx][jy][jz] (see volume.cu)
+    int pz, log_pz;
+    unsigned oddw_mask;   // bit s: component slot s is odd in the layer offset
+    unsigned imag3_mask;  // bit s: the three-level spectrum of slot s is imaginary
     // stage timing (grav_plan_set_timing)
     int timing;
     std::vector<cudaEvent_t> ev_pool;
@@ -121,6 +127,21 @@ struct Batch {
 // Thread-local error message and CUDA check helpers (capi.cu).
 void set_error(const char* fmt, ...);
 int cuda_fail(cudaError_t e, const char* what);
+
+// Plan helpers shared by the plane and equal-dimension plans (capi.cu).
+int ilog2(int v);
+// Smallest power of two >= max(4, 2n - 1).
+int circulant_size(int n);
+size_t round_up(size_t v, size_t m);
+// GRAV_EINVAL (with the message set) unless the sizes, spacings, height and
+// component mask are valid for a plan.
+int check_geometry(int nx, int ny, int nz, double dx, double dy, double dz, double h, unsigned components);
+int dev_alloc_raw(void** p, size_t bytes, const char* what);
+// Twiddle table W_T[e] = exp(-2 pi i e / T), T = 2^log_t, in FP64 (fp64 = 1)
+// or FP32, on the device.
+int build_twiddles(int log_t, int fp64, void** dev, size_t* bytes);
+// Frees every device buffer and event of the plan, and the plan.
+void free_plan(grav_plan* p);
 
 // ---- kernel generation (kernel_gen.cu) ----
 // mode 0: embed into a circulant array E[(c * nzc + n) * py + b][a] of size

@@ -1,0 +1,634 @@
+// Equal-dimension variant (Sec. 2.2, Eqs. 10-11): a station at the centre of
+// every cell, so the data are as three-dimensional as the mesh and G is
+// block Toeplitz in all three cell offsets (the block matrix of G_{t,n}
+// after Eq. 22): G(station (p,q,t), cell (l,m,n)) = K(l-p, m-q, n-t), with
+// (2nx-1)(2ny-1)(2nz-1) distinct values.
+//
+// The product is a three-level circulant embedding plus FFT: K(u,v,w) sits at
+// ((-u) mod Px, (-v) mod Py, (-w) mod Pz) (the correlation form of Eq. 19 on
+// every axis), each P a power of two >= 2n-1.  The embedded kernel is even or
+// odd in every axis (the reflection symmetries of Sec. 2.2; along w: gz, gxz
+// and gyz change sign when the station and the cell swap sides, the rest do
+// not), so its spectrum is purely real or purely imaginary and even or odd in
+// kx, ky and kz: the plan stores one real number per mirror triple,
+//   spec3[c][kx][jy][jz],  kx <= Px/2, jy <= Py/2, jz <= Pz/2,
+// with S_c(kx, ky, kz) = +-v (real) or +-i v (imaginary), the signs given by
+// the component's parity in y and z for ky > Py/2, kz > Pz/2, and the
+// 1/(Px Py Pz) of the inverse transforms folded in.
+//
+// Plan creation (FP64).  K(u,v,w) for a station at a cell centre is the
+// plane kernel of kernel_gen.cu for 2nz-1 "layers" j = w + nz - 1 seen from
+// the height h' = -(nz - 1/2) dz: its z-levels (nz - 1/2 - j) dz and
+// (nz - 3/2 - j) dz are the station-minus-corner depths (1/2 - w) dz and
+// (-1/2 - w) dz.  Per component and chunk of layers: generate and embed
+// (kernel_gen), transform the rows (x, row_r2c), transform the columns (y)
+// and keep the real or imaginary part of ky <= Py/2 per layer; then
+// transform each (kx, ky) sequence over the layers along z and keep the real
+// or imaginary part of kz <= Pz/2.
+//
+// Forward, per call (five passes through HBM; B = ncomp):
+//   A  x: row transforms of rho (R2C, row_r2c)          -> X[kx][n][y]
+//   B  y: column FFTs of every (kx, n) row (length Py)    -> U[kx][n][ky]
+//   C  z: per kx and tile of ky columns, FFT along n (length Pz), product with
+//         S_c, inverse FFT, the nz stations kept, for every component c
+//                                                         -> W[kx][c][t][ky]
+//   D  y: inverse column FFTs, the ny stations kept       -> V[kx][c][t][y]
+//   E  x: inverse row transforms (C2R, row_c2r)           -> out[c][t][y][x]
+// The adjoint runs the same passes from r[c][t][y][x], multiplies by the
+// conjugate spectra and sums over components in pass C (the transpose).
+#include <new>
+
+#include "fft_block.cuh"
+#include "grav_internal.h"
+
+namespace grav {
+
+namespace {
+
+constexpr int kVolMaxNx = 1024, kVolMaxNy = 1024, kVolMaxNz = 512;
+constexpr int kVolThreads = 256;
+// gz, gxz and gyz are odd in the layer offset w (the field of a cell below a
+// station is the mirror image of one above it with the vertical sense flipped).
+constexpr unsigned kOddWMask = 0x29u;
+__host__ __device__ constexpr bool odd_w(int c) { return (kOddWMask >> c) & 1u; }
+
+// Sequences per CTA of the row FFT kernels: about 64 KB (FP32) / 128 KB
+// (FP64) of shared memory.
+template <typename C> constexpr int rows_nseq(int logn) {
+    const int n = 8192 >> logn;
+    return n < 1 ? 1 : (n > 64 ? 64 : n);
+}
+// Columns per CTA of the z kernel: two buffers of TI sequences of Pz points.
+template <typename C> constexpr int z_tile(int logz) {
+    const int cap = sizeof(C) == 8 ? 32 : 16;
+    const int n = (sizeof(C) == 8 ? 8192 : 4096) >> logz;
+    return n < 1 ? 1 : (n > cap ? cap : n);
+}
+
+// ---------------------------------------------------------------------------
+// Pass B / D (and the plan's column step): FFTs of `rows` contiguous rows.
+//   in row k: in[k * in_stride + m], m < l_in (zero beyond); out row k:
+//   out[k * out_stride + m], m < l_out.
+template <typename C, int LOGN, int NSEQ, bool INV>
+__global__ void __launch_bounds__(kVolThreads) vol_rows_kernel(const C* __restrict__ in, size_t in_stride, int l_in,
+                                                               C* __restrict__ out, size_t out_stride, int l_out,
+                                                               long rows, const C* __restrict__ tw, int tw_shift) {
+    constexpr int N = 1 << LOGN, SSTR = seq_stride<C>(N);
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    C* buf = reinterpret_cast<C*>(smem_raw);
+    const int tid = threadIdx.x;
+    const long row0 = (long)blockIdx.x * NSEQ;
+    block_fft_from<C, LOGN, NSEQ, kVolThreads, INV>(buf, SSTR, tw, tw_shift, tid, [&](int s, int m) {
+        const long k = row0 + s;
+        return (k < rows && m < l_in) ? in[k * in_stride + m] : cmk<C>(0, 0);
+    });
+    for (int e = tid; e < NSEQ * l_out; e += kVolThreads) {
+        const int s = e / l_out, m = e - s * l_out;
+        const long k = row0 + s;
+        if (k < rows) out[k * out_stride + m] = buf[s * SSTR + sidx<C>(m)];
+    }
+}
+
+struct ZArgs {
+    int nz, py, kx_count, ncomp;
+    int jyc, jzc;          // stored spectra extents per kx: Py/2 + 1, Pz/2 + 1
+    unsigned imag3_mask;   // slot s: imaginary three-level spectrum
+    unsigned oddv_mask;    // slot s: odd in y
+    unsigned oddw_mask;    // slot s: odd in the layer offset
+    int tw_shift;          // log2(T / Pz)
+};
+
+// Pass C.  Forward (ADJ = false): in = U[kx][n][py], out = W[kx][c][t][py].
+// Adjoint: in = U'[kx][c][t][py], out = W'[kx][n][py] = sum_c conj(S_c) . in_c
+// transformed back.  One CTA per kx and tile of TI columns ky0 .. ky0 + TI.
+template <typename R, int LOGZ, int TI, bool ADJ>
+__global__ void __launch_bounds__(kVolThreads) vol_z_kernel(ZArgs a, const typename cplx<R>::type* __restrict__ in,
+                                                            typename cplx<R>::type* __restrict__ out,
+                                                            const R* __restrict__ spec3,
+                                                            const typename cplx<R>::type* __restrict__ tw) {
+    using C = typename cplx<R>::type;
+    constexpr int PZ = 1 << LOGZ, SSTR = seq_stride<C>(PZ), NT = kVolThreads;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    C* F = reinterpret_cast<C*>(smem_raw);
+    C* G = F + TI * SSTR;
+    const int tid = threadIdx.x;
+    const int kx = blockIdx.x, ky0 = blockIdx.y * TI;
+    const int nz = a.nz, py = a.py;
+
+    // column tile (TI columns of nz values, zero-padded to Pz) into buf
+    auto load_tile = [&](C* buf, const C* src) {
+        for (int e = tid; e < TI * PZ; e += NT) {
+            const int i = e % TI, n = e / TI;
+            C v = cmk<C>(0, 0);
+            if (n < nz && ky0 + i < py) v = src[(size_t)n * py + ky0 + i];
+            buf[i * SSTR + sidx<C>(n)] = v;
+        }
+    };
+    // spectrum value of slot c at (kx, ky0 + i, kz), as the real number v with
+    // S = v (real slot) or S = i v (imaginary slot)
+    auto spec_at = [&](int c, int i, int kz) -> R {
+        const int ky = ky0 + i;
+        const bool fy = ky > py / 2, fz = kz > PZ / 2;
+        const int jy = fy ? py - ky : ky, jz = fz ? PZ - kz : kz;
+        R v = spec3[(((size_t)c * a.kx_count + kx) * a.jyc + jy) * a.jzc + jz];
+        if ((fy && ((a.oddv_mask >> c) & 1u)) != (fz && ((a.oddw_mask >> c) & 1u))) v = -v;
+        return v;
+    };
+
+    if constexpr (!ADJ) {
+        load_tile(F, in + (size_t)kx * nz * py);
+        __syncthreads();
+        block_fft<C, LOGZ, TI, NT, false>(F, SSTR, tw, a.tw_shift, tid);
+        for (int c = 0; c < a.ncomp; ++c) {
+            const bool imag = (a.imag3_mask >> c) & 1u;
+            for (int e = tid; e < TI * PZ; e += NT) {
+                const int i = e / PZ, kz = e - i * PZ;
+                if (ky0 + i >= py) continue;
+                const R v = spec_at(c, i, kz);
+                const C f = F[i * SSTR + sidx<C>(kz)];
+                G[i * SSTR + sidx<C>(kz)] = imag ? cmk<C>(-v * f.y, v * f.x) : cmk<C>(v * f.x, v * f.y);
+            }
+            __syncthreads();
+            block_fft<C, LOGZ, TI, NT, true>(G, SSTR, tw, a.tw_shift, tid);
+            C* dst = out + (((size_t)kx * a.ncomp + c) * nz) * py + ky0;
+            for (int e = tid; e < TI * nz; e += NT) {
+                const int i = e % TI, t = e / TI;
+                if (ky0 + i < py) dst[(size_t)t * py + i] = G[i * SSTR + sidx<C>(t)];
+            }
+            __syncthreads();  // G is rewritten by the next component
+        }
+    } else {
+        for (int e = tid; e < TI * PZ; e += NT) {
+            const int i = e / PZ, kz = e - i * PZ;
+            G[i * SSTR + sidx<C>(kz)] = cmk<C>(0, 0);
+        }
+        for (int c = 0; c < a.ncomp; ++c) {
+            load_tile(F, in + (((size_t)kx * a.ncomp + c) * nz) * py);
+            __syncthreads();
+            block_fft<C, LOGZ, TI, NT, false>(F, SSTR, tw, a.tw_shift, tid);
+            const bool imag = (a.imag3_mask >> c) & 1u;
+            for (int e = tid; e < TI * PZ; e += NT) {
+                const int i = e / PZ, kz = e - i * PZ;
+                if (ky0 + i >= py) continue;
+                const R v = spec_at(c, i, kz);
+                const C f = F[i * SSTR + sidx<C>(kz)];
+                C& g = G[i * SSTR + sidx<C>(kz)];
+                // conj(S) f: S = v or S = i v
+                g = imag ? cmk<C>(g.x + v * f.y, g.y - v * f.x) : cmk<C>(g.x + v * f.x, g.y + v * f.y);
+            }
+            __syncthreads();  // F is reloaded for the next component
+        }
+        block_fft<C, LOGZ, TI, NT, true>(G, SSTR, tw, a.tw_shift, tid);
+        C* dst = out + (size_t)kx * nz * py + ky0;
+        for (int e = tid; e < TI * nz; e += NT) {
+            const int i = e % TI, n = e / TI;
+            if (ky0 + i < py) dst[(size_t)n * py + i] = G[i * SSTR + sidx<C>(n)];
+        }
+    }
+}
+
+// Plan creation, column step: y-FFT of the kernel row transforms
+// Ehat[kx][o][b] (o < cnt layers of one component, b < py) and the real
+// (imag2 = false) or imaginary part of ky <= Py/2, stored as
+// T[(kx * jyc + ky) * nzw + j0 + o].
+template <int LOGY, int NSEQ>
+__global__ void __launch_bounds__(kVolThreads) vol_spec_y_kernel(const double2* __restrict__ ehat, int cnt,
+                                                                 int kx_count, int j0, int nzw, bool imag2,
+                                                                 double* __restrict__ T,
+                                                                 const double2* __restrict__ tw, int tw_shift) {
+    constexpr int N = 1 << LOGY, SSTR = seq_stride<double2>(N), JYC = N / 2 + 1;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    double2* buf = reinterpret_cast<double2*>(smem_raw);
+    const int tid = threadIdx.x;
+    const long rows = (long)kx_count * cnt;
+    const long row0 = (long)blockIdx.x * NSEQ;
+    block_fft_from<double2, LOGY, NSEQ, kVolThreads, false>(buf, SSTR, tw, tw_shift, tid, [&](int s, int m) {
+        const long k = row0 + s;
+        return k < rows ? ehat[k * N + m] : cmk<double2>(0, 0);
+    });
+    for (int e = tid; e < NSEQ * JYC; e += kVolThreads) {
+        const int s = e / JYC, ky = e - s * JYC;
+        const long k = row0 + s;
+        if (k >= rows) continue;
+        const int kx = (int)(k / cnt), o = (int)(k - (long)kx * cnt);
+        const double2 v = buf[s * SSTR + sidx<double2>(ky)];
+        T[((size_t)kx * JYC + ky) * nzw + j0 + o] = imag2 ? v.y : v.x;
+    }
+}
+
+// Plan creation, z step: for every (kx, jy) row of T (2nz - 1 layer values,
+// j = w + nz - 1), embed K(w) at (-w) mod Pz, transform (length Pz), and keep
+// the real or imaginary part of kz <= Pz/2, scaled, as spec3[kx][jy][jz] of
+// one component (S = imag2 ? i T : T per layer, so the transform gives the
+// complex three-level spectrum itself).
+template <typename RO, int LOGZ, int NSEQ>
+__global__ void __launch_bounds__(kVolThreads) vol_spec_z_kernel(const double* __restrict__ T, long rows, int nz,
+                                                                 bool imag2, bool imag3, double scale,
+                                                                 RO* __restrict__ spec3,
+                                                                 const double2* __restrict__ tw, int tw_shift) {
+    constexpr int PZ = 1 << LOGZ, SSTR = seq_stride<double2>(PZ), JZC = PZ / 2 + 1;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    double2* buf = reinterpret_cast<double2*>(smem_raw);
+    const int tid = threadIdx.x;
+    const int nzw = 2 * nz - 1;
+    const long row0 = (long)blockIdx.x * NSEQ;
+    block_fft_from<double2, LOGZ, NSEQ, kVolThreads, false>(buf, SSTR, tw, tw_shift, tid, [&](int s, int m) {
+        const long k = row0 + s;
+        int w;
+        bool live = k < rows;
+        if (m <= nz - 1) w = -m;
+        else if (m >= PZ - nz + 1) w = PZ - m;
+        else live = false;
+        if (!live) return cmk<double2>(0, 0);
+        const double v = T[k * nzw + w + nz - 1];
+        return imag2 ? cmk<double2>(0, v) : cmk<double2>(v, 0);
+    });
+    for (int e = tid; e < NSEQ * JZC; e += kVolThreads) {
+        const int s = e / JZC, kz = e - s * JZC;
+        const long k = row0 + s;
+        if (k >= rows) continue;
+        const double2 v = buf[s * SSTR + sidx<double2>(kz)];
+        spec3[k * JZC + kz] = (RO)((imag3 ? v.y : v.x) * scale);
+    }
+}
+
+template <typename C, int LOGN, bool INV>
+cudaError_t rows_launch(const void* in, size_t in_stride, int l_in, void* out, size_t out_stride, int l_out, long rows,
+                        const void* tw, int tw_shift, cudaStream_t s) {
+    constexpr int NSEQ = rows_nseq<C>(LOGN);
+    constexpr auto k = vol_rows_kernel<C, LOGN, NSEQ, INV>;
+    const size_t smem = (size_t)NSEQ * seq_stride<C>(1 << LOGN) * sizeof(C);
+    cudaError_t e = ensure_smem_limit<k>();
+    if (e != cudaSuccess) return e;
+    const long blocks = (rows + NSEQ - 1) / NSEQ;
+    if (blocks == 0) return cudaSuccess;
+    k<<<(unsigned)blocks, kVolThreads, smem, s>>>((const C*)in, in_stride, l_in, (C*)out, out_stride, l_out, rows,
+                                                   (const C*)tw, tw_shift);
+    return cudaGetLastError();
+}
+
+#define GRAV_VOL_LOG_CASES(X) X(2) X(3) X(4) X(5) X(6) X(7) X(8) X(9) X(10) X(11)
+
+template <typename C, bool INV>
+cudaError_t launch_vol_rows(int logn, const void* in, size_t in_stride, int l_in, void* out, size_t out_stride,
+                            int l_out, long rows, const void* tw, int log_t, cudaStream_t s) {
+    switch (logn) {
+#define CASE(L) \
+    case L: return rows_launch<C, L, INV>(in, in_stride, l_in, out, out_stride, l_out, rows, tw, log_t - L, s);
+        GRAV_VOL_LOG_CASES(CASE)
+#undef CASE
+        default: return cudaErrorInvalidValue;
+    }
+}
+
+template <typename R, int LOGZ, bool ADJ>
+cudaError_t z_launch(const ZArgs& a, const void* in, void* out, const R* spec3, const void* tw, cudaStream_t s) {
+    using C = typename cplx<R>::type;
+    constexpr int TI = z_tile<C>(LOGZ);
+    constexpr auto k = vol_z_kernel<R, LOGZ, TI, ADJ>;
+    const size_t smem = (size_t)2 * TI * seq_stride<C>(1 << LOGZ) * sizeof(C);
+    cudaError_t e = ensure_smem_limit<k>();
+    if (e != cudaSuccess) return e;
+    k<<<dim3(a.kx_count, (a.py + TI - 1) / TI), kVolThreads, smem, s>>>(a, (const C*)in, (C*)out, spec3,
+                                                                       (const C*)tw);
+    return cudaGetLastError();
+}
+
+template <typename R, bool ADJ>
+cudaError_t launch_vol_z(int logz, const ZArgs& a, const void* in, void* out, const R* spec3, const void* tw,
+                         cudaStream_t s) {
+    switch (logz) {
+#define CASE(L) \
+    case L: return z_launch<R, L, ADJ>(a, in, out, spec3, tw, s);
+        GRAV_VOL_LOG_CASES(CASE)
+#undef CASE
+        default: return cudaErrorInvalidValue;
+    }
+}
+
+template <int LOGY>
+cudaError_t spec_y_launch(const void* ehat, int cnt, int kx_count, int j0, int nzw, bool imag2, double* T,
+                          const void* tw64, int log_t, cudaStream_t s) {
+    constexpr int NSEQ = rows_nseq<double2>(LOGY);
+    constexpr auto k = vol_spec_y_kernel<LOGY, NSEQ>;
+    const size_t smem = (size_t)NSEQ * seq_stride<double2>(1 << LOGY) * sizeof(double2);
+    cudaError_t e = ensure_smem_limit<k>();
+    if (e != cudaSuccess) return e;
+    const long rows = (long)kx_count * cnt;
+    k<<<(unsigned)((rows + NSEQ - 1) / NSEQ), kVolThreads, smem, s>>>((const double2*)ehat, cnt, kx_count, j0, nzw,
+                                                                       imag2, T, (const double2*)tw64, log_t - LOGY);
+    return cudaGetLastError();
+}
+
+template <typename RO, int LOGZ>
+cudaError_t spec_z_launch(const double* T, long rows, int nz, bool imag2, bool imag3, double scale, RO* spec3,
+                          const void* tw64, int log_t, cudaStream_t s) {
+    constexpr int NSEQ = rows_nseq<double2>(LOGZ);
+    constexpr auto k = vol_spec_z_kernel<RO, LOGZ, NSEQ>;
+    const size_t smem = (size_t)NSEQ * seq_stride<double2>(1 << LOGZ) * sizeof(double2);
+    cudaError_t e = ensure_smem_limit<k>();
+    if (e != cudaSuccess) return e;
+    k<<<(unsigned)((rows + NSEQ - 1) / NSEQ), kVolThreads, smem, s>>>(T, rows, nz, imag2, imag3, scale, spec3,
+                                                                       (const double2*)tw64, log_t - LOGZ);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_spec_y(int logy, const void* ehat, int cnt, int kx_count, int j0, int nzw, bool imag2, double* T,
+                          const void* tw64, int log_t, cudaStream_t s) {
+    switch (logy) {
+#define CASE(L) \
+    case L: return spec_y_launch<L>(ehat, cnt, kx_count, j0, nzw, imag2, T, tw64, log_t, s);
+        GRAV_VOL_LOG_CASES(CASE)
+#undef CASE
+        default: return cudaErrorInvalidValue;
+    }
+}
+
+template <typename RO>
+cudaError_t launch_spec_z(int logz, const double* T, long rows, int nz, bool imag2, bool imag3, double scale,
+                          RO* spec3, const void* tw64, int log_t, cudaStream_t s) {
+    switch (logz) {
+#define CASE(L) \
+    case L: return spec_z_launch<RO, L>(T, rows, nz, imag2, imag3, scale, spec3, tw64, log_t, s);
+        GRAV_VOL_LOG_CASES(CASE)
+#undef CASE
+        default: return cudaErrorInvalidValue;
+    }
+}
+
+// Per-call workspaces (complex elements of the plan's type): A holds X then
+// W (forward) or X' then W' (adjoint); B holds U then V (forward) or U' then
+// V' (adjoint).
+size_t vol_ws_a_elems(const grav_plan* p) {
+    const size_t kx = p->kx_count, nz = p->nz, nc = p->ncomp;
+    const size_t x = kx * nc * nz * p->ny_pad;  // X' (the larger of X and X')
+    const size_t w = kx * nc * nz * p->py;      // W (the larger of W and W')
+    return x > w ? x : w;
+}
+size_t vol_ws_b_elems(const grav_plan* p) {
+    const size_t kx = p->kx_count, nz = p->nz, nc = p->ncomp;
+    return kx * nc * nz * p->py;  // U' (the largest of U, U', V and V')
+}
+
+template <typename R>
+int make_spectra3(grav_plan* p) {
+    const int nzw = 2 * p->nz - 1;
+    const int jyc = p->py / 2 + 1, jzc = p->pz / 2 + 1;
+    // FP64 staging per chunk of layers of one component: the embedded
+    // kernels and their row transforms, bounded to about 2 GB; plus the
+    // column-step output T of one component.
+    const size_t per_layer = (size_t)p->py * p->px * sizeof(double) + (size_t)p->kx_count * p->py * 2 * sizeof(double);
+    int nzc = (int)(((size_t)2 << 30) / per_layer);
+    if (nzc < 1) nzc = 1;
+    if (nzc > nzw) nzc = nzw;
+    if (nzc > 65535) nzc = 65535;
+    void* tw64 = nullptr;
+    size_t tw64_bytes = 0;
+    int rc = GRAV_OK;
+    if (p->fp64) {
+        tw64 = p->tw;
+    } else if ((rc = build_twiddles(p->log_t, 1, &tw64, &tw64_bytes)) != GRAV_OK) {
+        return rc;
+    }
+    void *E = nullptr, *Ehat = nullptr, *T = nullptr;
+    const size_t e_bytes = (size_t)nzc * p->py * p->px * sizeof(double);
+    const size_t eh_bytes = (size_t)p->kx_count * nzc * p->py * 2 * sizeof(double);
+    const size_t t_bytes = (size_t)p->kx_count * jyc * nzw * sizeof(double);
+    if ((rc = dev_alloc_raw(&E, e_bytes, "kernel staging")) == GRAV_OK &&
+        (rc = dev_alloc_raw(&Ehat, eh_bytes, "kernel row-transform staging")) == GRAV_OK &&
+        (rc = dev_alloc_raw(&T, t_bytes, "kernel column-transform staging")) == GRAV_OK) {
+        cudaStream_t s;
+        cudaError_t ce = cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking);
+        if (ce != cudaSuccess) {
+            rc = cuda_fail(ce, "cudaStreamCreate");
+        } else {
+            // the plane generator with 2nz - 1 layers seen from h' = -(nz - 1/2) dz
+            const Geometry g{p->nx, p->ny, nzw, p->dx, p->dy, p->dz, -(p->nz - 0.5) * p->dz};
+            const double scale = 1.0 / ((double)p->px * (double)p->py * (double)p->pz);
+            for (int slot = 0; slot < p->ncomp && rc == GRAV_OK; ++slot) {
+                const int c = p->comp_id[slot];
+                const bool imag2 = odd_u(c) != odd_v(c);
+                const bool imag3 = (p->imag3_mask >> slot) & 1u;
+                for (int j0 = 0; j0 < nzw && rc == GRAV_OK; j0 += nzc) {
+                    const int j1 = j0 + nzc < nzw ? j0 + nzc : nzw;
+                    const int cnt = j1 - j0;
+                    if ((ce = cudaMemsetAsync(E, 0, (size_t)cnt * p->py * p->px * sizeof(double), s)) != cudaSuccess) {
+                        rc = cuda_fail(ce, "cudaMemsetAsync(kernel staging)");
+                        break;
+                    }
+                    if ((ce = launch_kernel_gen(g, 1u << c, j0, j1, 0, p->px, p->py, (double*)E, s)) != cudaSuccess) {
+                        rc = cuda_fail(ce, "kernel generation launch");
+                        break;
+                    }
+                    if ((ce = launch_row_r2c<double>(p->log_px, (const double*)E, (size_t)p->py * p->px, (size_t)p->px,
+                                                     p->px, p->py, cnt, Ehat, p->py, tw64, p->log_t, s)) !=
+                        cudaSuccess) {
+                        rc = cuda_fail(ce, "kernel row transform launch");
+                        break;
+                    }
+                    if ((ce = launch_spec_y(p->log_py, Ehat, cnt, p->kx_count, j0, nzw, imag2, (double*)T, tw64,
+                                            p->log_t, s)) != cudaSuccess) {
+                        rc = cuda_fail(ce, "kernel column transform launch");
+                        break;
+                    }
+                }
+                if (rc != GRAV_OK) break;
+                R* dst = (R*)p->spec + (size_t)slot * p->kx_count * jyc * jzc;
+                if ((ce = launch_spec_z<R>(p->log_pz, (const double*)T, (long)p->kx_count * jyc, p->nz, imag2, imag3,
+                                           scale, dst, tw64, p->log_t, s)) != cudaSuccess) {
+                    rc = cuda_fail(ce, "kernel layer transform launch");
+                    break;
+                }
+            }
+            ce = cudaStreamSynchronize(s);
+            if (rc == GRAV_OK && ce != cudaSuccess) rc = cuda_fail(ce, "plan construction");
+            cudaStreamDestroy(s);
+        }
+    }
+    cudaFree(E);
+    cudaFree(Ehat);
+    cudaFree(T);
+    if (!p->fp64) cudaFree(tw64);
+    return rc;
+}
+
+ZArgs z_args(const grav_plan* p) {
+    ZArgs a{};
+    a.nz = p->nz;
+    a.py = p->py;
+    a.kx_count = p->kx_count;
+    a.ncomp = p->ncomp;
+    a.jyc = p->py / 2 + 1;
+    a.jzc = p->pz / 2 + 1;
+    a.imag3_mask = p->imag3_mask;
+    a.oddv_mask = p->oddv_mask;
+    a.oddw_mask = p->oddw_mask;
+    a.tw_shift = p->log_t - p->log_pz;
+    return a;
+}
+
+template <typename R>
+int run_forward3d(grav_plan* p, const void* rho, void* out, cudaStream_t s) {
+    using C = typename cplx<R>::type;
+    const size_t kx = p->kx_count, nz = p->nz, nc = p->ncomp;
+    void* A = p->ws_a;
+    void* B = p->ws_b;
+    cudaError_t e;
+    // A: x
+    e = launch_row_r2c<R>(p->log_px, (const R*)rho, (size_t)p->ny * p->nx, (size_t)p->nx, p->nx, p->ny, p->nz, A,
+                          p->ny_pad, p->tw, p->log_t, s, Batch(), p->err_flag);
+    if (e != cudaSuccess) return cuda_fail(e, "equal-dimension forward: row transforms");
+    // B: y
+    e = launch_vol_rows<C, false>(p->log_py, A, p->ny_pad, p->ny, B, p->py, p->py, (long)(kx * nz), p->tw, p->log_t, s);
+    if (e != cudaSuccess) return cuda_fail(e, "equal-dimension forward: column transforms");
+    // C: z, product, inverse z
+    e = launch_vol_z<R, false>(p->log_pz, z_args(p), B, A, (const R*)p->spec, p->tw, s);
+    if (e != cudaSuccess) return cuda_fail(e, "equal-dimension forward: layer transforms");
+    // D: inverse y
+    e = launch_vol_rows<C, true>(p->log_py, A, p->py, p->py, B, p->ny_pad, p->ny, (long)(kx * nc * nz), p->tw,
+                                 p->log_t, s);
+    if (e != cudaSuccess) return cuda_fail(e, "equal-dimension forward: inverse column transforms");
+    // E: inverse x
+    e = launch_row_c2r<R>(p->log_px, B, nullptr, p->ny, (int)(nc * nz), p->ny_pad, (R*)out, (size_t)p->nx, p->nx,
+                          p->tw, p->log_t, s);
+    if (e != cudaSuccess) return cuda_fail(e, "equal-dimension forward: inverse row transforms");
+    return GRAV_OK;
+}
+
+template <typename R>
+int run_adjoint3d(grav_plan* p, const void* r, void* grad, cudaStream_t s) {
+    using C = typename cplx<R>::type;
+    const size_t kx = p->kx_count, nz = p->nz, nc = p->ncomp;
+    void* A = p->ws_a;
+    void* B = p->ws_b;
+    cudaError_t e;
+    e = launch_row_r2c<R>(p->log_px, (const R*)r, (size_t)p->ny * p->nx, (size_t)p->nx, p->nx, p->ny, (int)(nc * nz),
+                          A, p->ny_pad, p->tw, p->log_t, s, Batch(), p->err_flag);
+    if (e != cudaSuccess) return cuda_fail(e, "equal-dimension adjoint: row transforms");
+    e = launch_vol_rows<C, false>(p->log_py, A, p->ny_pad, p->ny, B, p->py, p->py, (long)(kx * nc * nz), p->tw,
+                                  p->log_t, s);
+    if (e != cudaSuccess) return cuda_fail(e, "equal-dimension adjoint: column transforms");
+    e = launch_vol_z<R, true>(p->log_pz, z_args(p), B, A, (const R*)p->spec, p->tw, s);
+    if (e != cudaSuccess) return cuda_fail(e, "equal-dimension adjoint: layer transforms");
+    e = launch_vol_rows<C, true>(p->log_py, A, p->py, p->py, B, p->ny_pad, p->ny, (long)(kx * nz), p->tw, p->log_t, s);
+    if (e != cudaSuccess) return cuda_fail(e, "equal-dimension adjoint: inverse column transforms");
+    e = launch_row_c2r<R>(p->log_px, B, nullptr, p->ny, p->nz, p->ny_pad, (R*)grad, (size_t)p->nx, p->nx, p->tw,
+                          p->log_t, s);
+    if (e != cudaSuccess) return cuda_fail(e, "equal-dimension adjoint: inverse row transforms");
+    return GRAV_OK;
+}
+
+int check_volume_call(grav_plan* plan, const void* in, void* out, const char* name) {
+    if (!plan || !in || !out) {
+        set_error("%s: null plan or buffer", name);
+        return GRAV_EINVAL;
+    }
+    if (plan->kind != 1) {
+        set_error("%s: the plan was made by grav_plan_create, not grav_plan_create3d", name);
+        return GRAV_EINVAL;
+    }
+    return GRAV_OK;
+}
+
+}  // namespace
+
+}  // namespace grav
+
+using namespace grav;
+
+extern "C" {
+
+grav_plan* grav_plan_create3d(int nx, int ny, int nz, double dx, double dy, double dz, unsigned components) {
+    set_error("%s", "");
+    if (check_geometry(nx, ny, nz, dx, dy, dz, 1.0, components)) return nullptr;
+    if (nx > kVolMaxNx || ny > kVolMaxNy || nz > kVolMaxNz) {
+        set_error("equal-dimension mesh %dx%dx%d beyond %dx%dx%d", nx, ny, nz, kVolMaxNx, kVolMaxNy, kVolMaxNz);
+        return nullptr;
+    }
+    grav_plan* p = new (std::nothrow) grav_plan();
+    if (!p) {
+        set_error("host allocation of the plan failed");
+        return nullptr;
+    }
+    p->kind = 1;
+    p->nx = nx; p->ny = ny; p->nz = nz;
+    p->dx = dx; p->dy = dy; p->dz = dz; p->h = 0.0;
+    p->comps = components & kCompBits;
+    p->fp64 = (components & GRAV_FP64_SPECTRAL) ? 1 : 0;
+    for (int c = 0; c < kMaxComp; ++c) {
+        if (p->comps & (1u << c)) {
+            const int s = p->ncomp++;
+            p->comp_id[s] = c;
+            if (odd_u(c) != odd_v(c)) p->imag_mask |= 1u << s;
+            if (odd_v(c)) p->oddv_mask |= 1u << s;
+            if (odd_w(c)) p->oddw_mask |= 1u << s;
+            if ((int)odd_u(c) + (int)odd_v(c) + (int)odd_w(c) == 1 ||
+                (int)odd_u(c) + (int)odd_v(c) + (int)odd_w(c) == 3)
+                p->imag3_mask |= 1u << s;
+        }
+    }
+    p->px = circulant_size(nx);
+    p->py = circulant_size(ny);
+    p->pz = circulant_size(nz);
+    p->log_px = ilog2(p->px);
+    p->log_py = ilog2(p->py);
+    p->log_pz = ilog2(p->pz);
+    p->log_t = p->log_px;
+    if (p->log_py > p->log_t) p->log_t = p->log_py;
+    if (p->log_pz > p->log_t) p->log_t = p->log_pz;
+    p->kx_count = p->px / 2 + 1;
+    p->ny_pad = (int)round_up((size_t)ny, 4);
+    cudaGetDevice(&p->device);
+
+    const size_t real = p->fp64 ? sizeof(double) : sizeof(float);
+    p->spec_bytes = (size_t)p->ncomp * p->kx_count * (p->py / 2 + 1) * (p->pz / 2 + 1) * real;
+    p->ws_a_bytes = vol_ws_a_elems(p) * 2 * real;
+    p->ws_b_bytes = vol_ws_b_elems(p) * 2 * real;
+
+    size_t free_b = 0, total_b = 0;
+    cudaError_t ce = cudaMemGetInfo(&free_b, &total_b);
+    if (ce != cudaSuccess) {
+        cuda_fail(ce, "cudaMemGetInfo");
+        delete p;
+        return nullptr;
+    }
+    const size_t need = p->spec_bytes + p->ws_a_bytes + p->ws_b_bytes;
+    if (need > free_b) {
+        set_error("plan needs %zu bytes of device memory, %zu free", need, free_b);
+        delete p;
+        return nullptr;
+    }
+    int rc = build_twiddles(p->log_t, p->fp64, &p->tw, &p->tw_bytes);
+    if (!rc) rc = dev_alloc_raw(&p->spec, p->spec_bytes, "kernel spectra");
+    if (!rc) rc = dev_alloc_raw(&p->ws_a, p->ws_a_bytes, "workspace A");
+    if (!rc) rc = dev_alloc_raw(&p->ws_b, p->ws_b_bytes, "workspace B");
+    if (!rc) rc = dev_alloc_raw((void**)&p->err_flag, 256, "error flag");
+    if (!rc) {
+        cudaError_t me = cudaMemset(p->err_flag, 0, 256);
+        if (me != cudaSuccess) rc = cuda_fail(me, "cudaMemset(error flag)");
+    }
+    if (!rc) rc = p->fp64 ? make_spectra3<double>(p) : make_spectra3<float>(p);
+    if (rc) {
+        free_plan(p);
+        return nullptr;
+    }
+    return p;
+}
+
+int grav_forward3d(grav_plan* plan, const void* rho_dev, void* out_dev, void* stream) {
+    int rc = check_volume_call(plan, rho_dev, out_dev, "grav_forward3d");
+    if (rc) return rc;
+    cudaStream_t s = (cudaStream_t)stream;
+    return plan->fp64 ? run_forward3d<double>(plan, rho_dev, out_dev, s)
+                      : run_forward3d<float>(plan, rho_dev, out_dev, s);
+}
+
+int grav_adjoint3d(grav_plan* plan, const void* r_dev, void* grad_dev, void* stream) {
+    int rc = check_volume_call(plan, r_dev, grad_dev, "grav_adjoint3d");
+    if (rc) return rc;
+    cudaStream_t s = (cudaStream_t)stream;
+    return plan->fp64 ? run_adjoint3d<double>(plan, r_dev, grad_dev, s)
+                      : run_adjoint3d<float>(plan, r_dev, grad_dev, s);
+}
+
+}  // extern "C"

@@ -104,6 +104,53 @@ class Plan:
         self.close()
 
 
+class Plan3D(Plan):
+    """Equal-dimension plan (Sec. 2.2, Eqs. 10-11): a station at the centre
+    of every cell; three-level circulant spectra resident on the current
+    CUDA device.  mesh: (nx, ny, nz, dx, dy, dz[, h]) or an object with those
+    attributes (h, if given, is not used)."""
+
+    def __init__(self, mesh, components: int = capi.GRAV_ALL6, fp64: bool = False):
+        if hasattr(mesh, "tuple"):
+            mesh = mesh.tuple()
+        nx, ny, nz, dx, dy, dz = mesh[:6]
+        self.mesh = (int(nx), int(ny), int(nz), float(dx), float(dy), float(dz), 0.0)
+        self.components = int(components) & capi.GRAV_COMP_BITS
+        self.fp64 = bool(fp64)
+        if not torch.cuda.is_available():
+            raise RuntimeError("libgravfft needs a CUDA device")
+        self.device = torch.device("cuda", torch.cuda.current_device())
+        flags = self.components | (capi.GRAV_FP64_SPECTRAL if fp64 else 0)
+        self._h = capi.grav_plan_create3d(*self.mesh[:6], flags)
+        self.ncomp = len(capi.comp_list(self.components))
+        self.dtype = torch.float64 if fp64 else torch.float32
+        info = capi.grav_plan_info(self._h)
+        self.px, self.py, self.pz = info.px, info.py, info.pz
+        self.spectra_bytes = int(info.spectra_bytes)
+        self.workspace_bytes = int(info.workspace_bytes)
+        self.nbytes = capi.grav_plan_bytes(self._h)
+
+    def forward(self, rho: torch.Tensor, out: torch.Tensor | None = None, stream=None) -> torch.Tensor:
+        """d_c at every cell centre; rho [nz][ny][nx] -> [ncomp][nz][ny][nx]."""
+        nx, ny, nz = self.mesh[:3]
+        self._check(rho, (nz, ny, nx), "rho")
+        if out is None:
+            out = torch.empty((self.ncomp, nz, ny, nx), dtype=self.dtype, device=self.device)
+        self._check(out, (self.ncomp, nz, ny, nx), "out")
+        capi.grav_forward3d(self._h, rho.data_ptr(), out.data_ptr(), self._stream(stream))
+        return out
+
+    def adjoint(self, r: torch.Tensor, out: torch.Tensor | None = None, stream=None) -> torch.Tensor:
+        """sum_c G_c^T r_c; r [ncomp][nz][ny][nx] -> [nz][ny][nx]."""
+        nx, ny, nz = self.mesh[:3]
+        self._check(r, (self.ncomp, nz, ny, nx), "r")
+        if out is None:
+            out = torch.empty((nz, ny, nx), dtype=self.dtype, device=self.device)
+        self._check(out, (nz, ny, nx), "out")
+        capi.grav_adjoint3d(self._h, r.data_ptr(), out.data_ptr(), self._stream(stream))
+        return out
+
+
 def kernel_values(mesh, components: int, device=None, stream=None) -> torch.Tensor:
     """The FP64 kernel over the offset grid, [ncomp][nz][2ny-1][2nx-1] (Eq. 10)."""
     if hasattr(mesh, "tuple"):

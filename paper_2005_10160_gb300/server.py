@@ -67,6 +67,7 @@ class _Slot:
         self.stream = torch.cuda.Stream(device=device)
         self.busy = False
         self.event = None
+        self.start = None  # timing event recorded on the slot's stream before its batch
         self.batch: list[Request] = []
         self.buffers = ()
         self.nbytes = 0
@@ -98,6 +99,13 @@ class Server:
         self.completed: list[Request] = []
         self.batches_run = 0
         self.graph_replays = 0
+        self.max_busy_slots = 0
+        # device time line: every batch's [start, end] in ms after the
+        # reference event, from events on the slot streams (one GPU clock)
+        self.device_intervals: list[tuple[float, float, int]] = []
+        self._ref_event = torch.cuda.Event(enable_timing=True)
+        with torch.cuda.device(self.device):
+            self._ref_event.record(torch.cuda.current_stream(self.device))
         self._stop = False
         self._thread = threading.Thread(target=self._loop, name="grav-server", daemon=True)
         self._thread.start()
@@ -149,7 +157,23 @@ class Server:
         return {"requests": int(lat.size), "p50_ms": float(np.percentile(lat, 50) * 1e3),
                 "p99_ms": float(np.percentile(lat, 99) * 1e3), "mean_ms": float(lat.mean() * 1e3),
                 "req_per_s": float(lat.size / span) if span > 0 else None, "batches": self.batches_run,
-                "graph_replays": self.graph_replays}
+                "graph_replays": self.graph_replays, "max_busy_slots": self.max_busy_slots,
+                "max_concurrent_on_device": self.max_concurrent_on_device()}
+
+    def max_concurrent_on_device(self) -> int:
+        """Largest number of batches whose device intervals (from the event
+        before a batch's first kernel to the event after its last, on its
+        slot's stream) overlap at one instant."""
+        marks = []
+        for t0, t1, _ in self.device_intervals:
+            marks.append((t0, 1))
+            marks.append((t1, -1))
+        marks.sort(key=lambda m: (m[0], m[1]))  # an end before a start at the same instant
+        best = cur = 0
+        for _, d in marks:
+            cur += d
+            best = max(best, cur)
+        return best
 
     # -------------------------------------------------------------- internals
     def _plan(self, key) -> Plan | None:
@@ -271,6 +295,8 @@ class Server:
             for r in batch:  # inputs were produced on the submitting thread's stream
                 slot.stream.wait_event(r.ready)
                 r.data.record_stream(slot.stream)
+            start = torch.cuda.Event(enable_timing=True)
+            start.record(slot.stream)
             if use_graph:
                 entry = slot.graphs.get(gkey)
                 if entry is None and self.graph_used + B * (b_in + b_out + b_ws) <= self.graph_memory:
@@ -292,14 +318,16 @@ class Server:
                 call(plan.handle, B, inp.data_ptr(), out.data_ptr(), ws_ptr, slot.stream.cuda_stream)
                 slot.buffers = (inp, ws)
                 slot.nbytes = B * (b_in + b_out + b_ws)
-            ev = torch.cuda.Event()
+            ev = torch.cuda.Event(enable_timing=True)
             ev.record(slot.stream)
         self.used += slot.nbytes
         slot.out = out
         slot.event = ev
+        slot.start = start
         slot.batch = batch
         slot.busy = True
         self.batches_run += 1
+        self.max_busy_slots = max(self.max_busy_slots, sum(s.busy for s in self.slots))
 
     def _capture(self, slot, plan, call, B, in_shape, out_shape, dt, b_ws):
         inp = torch.zeros((B,) + in_shape, dtype=dt, device=self.device)
@@ -317,6 +345,9 @@ class Server:
 
     def _finish(self, slot: _Slot):
         t = time.perf_counter()
+        if slot.start is not None:
+            self.device_intervals.append((self._ref_event.elapsed_time(slot.start),
+                                          self._ref_event.elapsed_time(slot.event), slot.index))
         for i, r in enumerate(slot.batch):
             r.result = slot.out[i]
             r.t_done = t
@@ -324,7 +355,8 @@ class Server:
             r.done.set()
         self.plan_users[slot.batch[0].key] -= 1
         self.used -= slot.nbytes
-        slot.busy, slot.event, slot.batch, slot.buffers, slot.out, slot.nbytes = False, None, [], (), None, 0
+        slot.busy, slot.event, slot.start, slot.batch, slot.buffers, slot.out, slot.nbytes = (False, None, None, [], (),
+                                                                                            None, 0)
 
     def _loop(self):
         torch.cuda.set_device(self.device)

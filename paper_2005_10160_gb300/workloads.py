@@ -15,6 +15,8 @@ Workloads (the paper's experiments are all synthetic, Secs. 3.1-3.2):
 * ``grf1024``   1024x1024x100 cells of 50x50x25 m, stations 10 m up, a
                 smooth Gaussian random field (std 200, correlation length 20
                 cells) stored as float32.
+* ``boxes1024`` the grf1024 mesh with three seeded boxes of +300, -200 and
+                +150 (a field known in closed form at every station).
 * ``boxes512``  512x512x64 cubes of 20 m, stations 10 m up, three boxes of
                 +400, -300 and +250.
 * ``cube40``    the accuracy model of Sec. 3.1: a 300 m cube with its top at
@@ -127,6 +129,20 @@ def grf1024(nx=1024, ny=1024, nz=100, corr_cells=20.0, std=200.0, device="cpu"):
     field = field - field.mean()
     field = field * (std / field.std())
     return mesh, field.to(torch.float32).contiguous()
+
+
+def boxes1024():
+    """The grf1024 mesh (1024x1024x100 cells of 50x50x25 m, stations 10 m
+    up) holding three seeded boxes of +300, -200 and +150 kg/m^3 (extents up
+    to a quarter of each axis): a density whose field at every station is the
+    sum of three whole-box closed forms."""
+    mesh = grf_mesh()
+    rng = rng_for(6)
+    boxes = []
+    for d in (300.0, -200.0, 150.0):
+        b = random_boxes(mesh, 1, rng, 1.0)[0]
+        boxes.append((*b[:6], d))
+    return mesh, paint_boxes(mesh, boxes, np.float32), boxes
 
 
 def boxes512():

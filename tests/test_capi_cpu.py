@@ -64,6 +64,27 @@ def test_null_plan_and_buffers_are_rejected(gravlib):
     assert L.grav_forward_static_scratch(None, None, None, None) == capi.GRAV_EINVAL
     rc, _ = capi.grav_selftest_bounded_wait(0.0)
     assert rc == capi.GRAV_EINVAL
+    assert L.grav_forward3d(None, None, None, None) == capi.GRAV_EINVAL
+    assert L.grav_adjoint3d(None, None, None, None) == capi.GRAV_EINVAL
+
+
+@pytest.mark.parametrize(
+    "args,needle",
+    [
+        ((0, 4, 4, 1.0, 1.0, 1.0, 1), "mesh size"),
+        ((4, 4, 4, 1.0, 0.0, 1.0, 1), "cell sizes"),
+        ((4, 4, 4, 1.0, 1.0, 1.0, 0), "component"),
+        ((4, 4, 4, 1.0, 1.0, 1.0, 0x1FF), "more than 8 components"),
+        ((1025, 4, 4, 1.0, 1.0, 1.0, 1), "equal-dimension mesh"),
+        ((4, 4, 513, 1.0, 1.0, 1.0, 1), "equal-dimension mesh"),
+    ],
+)
+def test_plan_create3d_rejects_bad_arguments(gravlib, args, needle):
+    """Argument checks of the equal-dimension plan, before any device call."""
+    with pytest.raises(capi.GravError) as ei:
+        capi.grav_plan_create3d(*args)
+    assert ei.value.code == capi.GRAV_EINVAL
+    assert needle in str(ei.value)
 
 
 def _c_values(tmp_path, body):

@@ -154,6 +154,16 @@ def test_paper_cube_model(gravlib, orc):
     assert np.all(err <= 1e-12), err
     got32 = run_forward(mesh.tuple(), ALL7, rho.astype(np.float32), fp64=False)
     assert np.all(rel_errors(got32, ref, ALL7) <= TOL32)
+    # element-wise, in mGal (gz) and Eotvos (gradients), against each component's
+    # peak over the 40 x 40 stations: FP64 1e-10, FP32 2e-5 (the bounds of the
+    # full-size tests)
+    units = np.array([1e5] + [1e9] * 6)[:, None]
+    peak = np.abs(ref.reshape(7, -1) * units).max(axis=1)
+    max64 = np.abs((got - ref).reshape(7, -1) * units).max(axis=1)
+    max32 = np.abs((got32 - ref).reshape(7, -1) * units).max(axis=1)
+    print("cube max abs FP64", max64, "FP32", max32, "peak", peak)
+    assert np.all(max64 <= 1e-10 * peak), (max64, peak)
+    assert np.all(max32 <= 2e-5 * peak), (max32, peak)
 
 
 def test_boxes256_fp64_vs_oracle_and_superposition(gravlib, orc):

@@ -47,25 +47,85 @@ def _rel(a, b):
     return float((a.double() - b.double()).norm() / b.double().norm())
 
 
-def test_results_same_alone_and_in_the_mix(gravlib):
+def _oracle_sample(orc, kind, mesh, data, got, rng):
+    """Relative L2 error of a served result against the CPU oracle's direct
+    summation at 8 sampled stations (forward, per component) or cells
+    (adjoint)."""
+    if kind == "forward":
+        st = W.station_subset(mesh, 8, rng)
+        want = orc.forward(mesh.tuple(), capi.GRAV_ALL6, data.double().numpy(), stations=st)
+        have = got.reshape(6, -1)[:, st].double().numpy()
+        return np.linalg.norm(have - want, axis=1) / np.linalg.norm(want, axis=1)
+    cells = rng.choice(mesh.nx * mesh.ny * mesh.nz, 8, replace=False)
+    want = orc.adjoint(mesh.tuple(), capi.GRAV_ALL6, data.double().numpy(), cells=cells)
+    have = got.reshape(-1)[cells].double().numpy()
+    return np.array([np.linalg.norm(have - want) / np.linalg.norm(want)])
+
+
+def test_results_same_alone_and_in_the_mix(gravlib, orc):
+    """Requests arrive in bursts of 8 (so that several batches are in flight
+    on the slots' streams at once) on three meshes, forward and adjoint
+    mixed.  Every served result equals the same request run alone (<= 2e-5)
+    and the CPU oracle at sampled stations or cells (FP32 bar, 2e-5), and
+    the device time line shows batches overlapping."""
     rng = np.random.default_rng(5)
     inputs = _inputs(rng, 48)
     srv = Server(hbm_budget=8 << 30, slots=4, max_batch=4)
     try:
         reqs = []
-        for kind, mesh, data in inputs:
-            reqs.append(srv.submit(kind, mesh, data.cuda()))
-            time.sleep(float(rng.exponential(0.002)))  # Poisson arrivals, mean 2 ms
+        for b in range(0, len(inputs), 8):
+            # a burst of 8 enters the queue at once, so that one sweep of the
+            # loop admits a batch into every free slot
+            with srv.lock:
+                reqs += [srv.submit(kind, mesh, data.cuda()) for kind, mesh, data in inputs[b:b + 8]]
+            time.sleep(float(rng.exponential(0.004)))  # Poisson gaps between bursts
         srv.drain()
         mixed = [r.wait(60).cpu() for r in reqs]
         stats = srv.stats()
     finally:
         srv.close()
+    srng = np.random.default_rng(55)
     for (kind, mesh, data), got in zip(inputs, mixed):
         ref = _alone(kind, mesh, data)
         assert _rel(got, ref) <= 2e-5, (kind, mesh)
+        err = _oracle_sample(orc, kind, mesh, data, got, srng)
+        assert np.all(err <= 2e-5), (kind, mesh, err)
     assert stats["requests"] == len(inputs)
     assert np.isfinite(stats["p50_ms"]) and stats["p99_ms"] >= stats["p50_ms"]
+    assert stats["max_busy_slots"] >= 2, stats
+
+
+def test_batches_on_different_slots_overlap_on_the_device(gravlib):
+    """Four batches (forward and adjoint on two meshes, four requests each)
+    admitted in one sweep run on four slot streams; their intervals on the
+    device time line (events before and after each batch) overlap, and each
+    result equals the request run alone."""
+    meshes = [W.Mesh(256, 256, 32, 20.0, 20.0, 20.0, 10.0), W.Mesh(200, 180, 24, 20.0, 20.0, 20.0, 10.0)]
+    rng = np.random.default_rng(12)
+    groups = []
+    for m in meshes:
+        groups.append([("forward", m, torch.as_tensor(W.serving_density(m, rng), dtype=torch.float32))
+                       for _ in range(4)])
+        groups.append([("adjoint", m, torch.as_tensor(rng.normal(size=(6, m.ny, m.nx)), dtype=torch.float32))
+                       for _ in range(4)])
+    srv = Server(hbm_budget=16 << 30, slots=4, max_batch=4, graph_bytes_limit=0)
+    try:
+        for g in groups:  # build the plans first
+            srv.submit(g[0][0], g[0][1], g[0][2].cuda())
+        srv.drain()
+        srv.device_intervals.clear()
+        with srv.lock:
+            reqs = [srv.submit(kind, m, d.cuda()) for g in groups for kind, m, d in g]
+        srv.drain()
+        outs = [r.wait(60).cpu() for r in reqs]
+        stats = srv.stats()
+    finally:
+        srv.close()
+    assert stats["max_busy_slots"] == 4, stats
+    assert stats["max_concurrent_on_device"] >= 2, (stats, srv.device_intervals)
+    items = [it for g in groups for it in g]
+    for (kind, m, d), got in zip(items, outs):
+        assert _rel(got, _alone(kind, m, d)) <= 2e-5, (kind, m)
 
 
 def test_same_plan_requests_are_batched_and_replayed_from_graphs(gravlib):

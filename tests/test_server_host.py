@@ -34,6 +34,7 @@ class FakePlan:
 class FakeSlot:
     def __init__(self, index):
         self.index, self.busy, self.batch, self.out, self.nbytes, self.graphs = index, False, [], None, 0, {}
+        self.start = self.event = None
 
 
 class HostServer(S.Server):
@@ -50,6 +51,7 @@ class HostServer(S.Server):
         self.slots = [FakeSlot(i) for i in range(slots)]
         self.ids = itertools.count()
         self.completed, self.batches_run, self.graph_replays = [], 0, 0
+        self.max_busy_slots, self.device_intervals = 0, []
         self.device = torch.device("cpu")
         self.req_bytes = req_bytes
         self.launched = []
@@ -187,3 +189,15 @@ def test_plan_size_estimate_counts_the_compressed_spectra():
     workspaces = 2 * 1025 * 100 * 1024 * 8 + 2 * 1025 * 6 * 1024 * 8
     assert est == spectra + workspaces + 2048 * 8 + 256
     assert S.Server._plan_bytes_estimate((1024, 1024, 100, 50.0, 50.0, 25.0, 10.0), capi.GRAV_ALL6, True) > 2 * spectra
+
+
+def test_device_overlap_counts_intervals_that_share_an_instant():
+    """max_concurrent_on_device: the largest number of batch intervals on the
+    device time line that contain one instant; touching ends do not count."""
+    srv = HostServer(budget=1 << 20)
+    srv.device_intervals = [(0.0, 1.0, 0), (0.5, 2.0, 1), (1.0, 3.0, 0), (1.5, 1.8, 2), (5.0, 6.0, 1)]
+    assert srv.max_concurrent_on_device() == 3  # (0.5, 2), (1, 3) and (1.5, 1.8) at t = 1.6
+    srv.device_intervals = [(0.0, 1.0, 0), (1.0, 2.0, 1)]
+    assert srv.max_concurrent_on_device() == 1
+    srv.device_intervals = []
+    assert srv.max_concurrent_on_device() == 0
