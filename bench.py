@@ -63,8 +63,12 @@ def parse():
     ap.add_argument("--serve-requests", type=int, default=10000,
                     help="requests in the serving leg (Poisson arrivals, 0 to skip)")
     ap.add_argument("--serve-rate", type=float, default=200.0, help="mean arrival rate of the serving leg (1/s)")
+    ap.add_argument("--burst-requests", type=int, default=2000,
+                    help="requests in the burst serving leg (2000/s, two station heights; 0 to skip)")
     ap.add_argument("--equal-dim", default="1024,1024,100",
                     help="nx,ny,nz of the equal-dimension leg (grf1024 geometry; 'none' to skip)")
+    ap.add_argument("--equal-dim-only", action="store_true",
+                    help="run only the equal-dimension leg and print its record (profiling)")
     return ap.parse_args()
 
 
@@ -243,11 +247,12 @@ def cpu_density_sample(mesh, n_layers):
     return rho[:n_layers].float().cpu().numpy()
 
 
-def serving_leg(n_requests: int, rate: float):
+def serving_leg(n_requests: int, rate: float, heights=(10.0,)):
     """Poisson stream of forward/adjoint requests (50/50) on the four serving
     meshes (64^2x16, 128^2x32, 256^2x32, 512^2x64 of 20 m cubes, random-box
-    densities, N(0,1) adjoint inputs) through the continuous-batching server;
-    plans are built during a warm-up.  Latency is submission to completion."""
+    densities, N(0,1) adjoint inputs), each seen from the given station
+    heights, through the continuous-batching server; plans are built during
+    a warm-up.  Latency is submission to completion."""
     import numpy as np
     import torch
 
@@ -255,7 +260,10 @@ def serving_leg(n_requests: int, rate: float):
     from paper_2005_10160_gb300.server import Server
 
     rng = np.random.default_rng(workloads.SEED_BASE + 5)
-    meshes = [workloads.serving_mesh(i) for i in range(4)]
+    meshes = []
+    for i in range(4):
+        m = workloads.serving_mesh(i)
+        meshes += [workloads.Mesh(m.nx, m.ny, m.nz, m.dx, m.dy, m.dz, h) for h in heights]
     pool = {}
     for i, m in enumerate(meshes):
         pool[(i, "forward")] = [torch.as_tensor(workloads.serving_density(m, rng), device="cuda") for _ in range(4)]
@@ -267,7 +275,8 @@ def serving_leg(n_requests: int, rate: float):
                 srv.submit(kind, m, pool[(i, kind)][0])
         srv.drain()
         srv.completed.clear()
-        srv.batches_run = srv.graph_replays = 0
+        srv.device_intervals.clear()
+        srv.batches_run = srv.graph_replays = srv.cross_plan_batches = srv.max_busy_slots = 0
         t0 = time.perf_counter()
         t_next = t0
         pairs = 0.0
@@ -275,7 +284,7 @@ def serving_leg(n_requests: int, rate: float):
         swept = 0
         for _ in range(n_requests):
             t_next += float(rng.exponential(1.0 / rate))
-            i = int(rng.integers(4))
+            i = int(rng.integers(len(meshes)))
             kind = "forward" if rng.random() < 0.5 else "adjoint"
             m = meshes[i]
             delay = t_next - time.perf_counter()
@@ -296,7 +305,7 @@ def serving_leg(n_requests: int, rate: float):
         srv.close()
     st.update({"rate_per_s": rate, "pairs_per_s": pairs / span,
                "workload": "Poisson 50/50 forward/adjoint on 64^2x16, 128^2x32, 256^2x32, 512^2x64 (20 m cubes), "
-                           "FP32 spectra, plans resident"})
+                           f"stations {', '.join(f'{h:g}' for h in heights)} m up, FP32 spectra, plans resident"})
     return st
 
 
@@ -393,6 +402,17 @@ def run_reference(args):
 def run_ours(args):
     import numpy as np
     import torch
+
+    if args.equal_dim_only:
+        from paper_2005_10160_gb300 import build as gbuild
+        from paper_2005_10160_gb300 import capi
+
+        gbuild.build()
+        capi.lib()
+        torch.cuda.set_device(0)
+        print(json.dumps({"equal_dim": equal_dim_leg(args.equal_dim, torch.device("cuda", 0), hbm_peak()[0])}),
+              flush=True)
+        return 0
 
     from paper_2005_10160_gb300 import build as gbuild
     from paper_2005_10160_gb300 import capi, workloads
@@ -620,6 +640,8 @@ def run_ours(args):
     if rank == 0 and args.serve_requests > 0:
         plan.close()
         serving = serving_leg(args.serve_requests, args.serve_rate)
+        if args.burst_requests > 0:
+            serving = {**serving, "burst": serving_leg(args.burst_requests, 2000.0, heights=(10.0, 50.0))}
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline and args.workload == "grf1024":

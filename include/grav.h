@@ -144,6 +144,27 @@ int grav_forward_batch(grav_plan* plan, int batch, const void* rho_dev, void* ou
 int grav_adjoint_batch(grav_plan* plan, int batch, const void* r_dev, void* grad_dev, void* workspace_dev,
                        void* stream);
 
+/* Forward of `batch` requests on `batch` plans (one plan per request) with
+ * one launch per stage (Eq. 21 for each).  The plans may differ only in their
+ * kernel spectra, i.e. in cell sizes and station height: mesh sizes,
+ * components and precision must be equal (a serving loop batches requests on
+ * the same model seen from several heights this way).
+ *   batch          1 .. 16
+ *   plans          host array of `batch` plans made by grav_plan_create
+ *   rho_dev        device [batch][nz][ny][nx], request b on plans[b]
+ *   out_dev        device [batch][ncomp][ny][nx]
+ *   workspace_dev  device scratch of batch * grav_workspace_bytes(plans[0])
+ *                  bytes, 256-byte aligned, owned by the caller (required)
+ * Returns GRAV_OK, GRAV_EINVAL (null argument, plans that differ in more
+ * than their spectra) or GRAV_ECUDA. */
+int grav_forward_batch_plans(int batch, grav_plan* const* plans, const void* rho_dev, void* out_dev,
+                             void* workspace_dev, void* stream);
+
+/* Adjoint counterpart: r_dev [batch][ncomp][ny][nx] -> grad_dev
+ * [batch][nz][ny][nx], request b on plans[b]; rules as above. */
+int grav_adjoint_batch_plans(int batch, grav_plan* const* plans, const void* r_dev, void* grad_dev,
+                             void* workspace_dev, void* stream);
+
 /* Release the plan and its device memory (waits for the device first).
  * NULL is ignored. */
 void grav_plan_destroy(grav_plan* plan);

@@ -46,6 +46,8 @@ EXPORTED = (
     "grav_plan_create3d",
     "grav_forward3d",
     "grav_adjoint3d",
+    "grav_forward_batch_plans",
+    "grav_adjoint_batch_plans",
 )
 
 
@@ -112,6 +114,10 @@ def lib() -> ctypes.CDLL:
             L.grav_forward_batch.restype = i
             L.grav_adjoint_batch.argtypes = [p, i, p, p, p, p]
             L.grav_adjoint_batch.restype = i
+            L.grav_forward_batch_plans.argtypes = [i, ctypes.POINTER(p), p, p, p, p]
+            L.grav_forward_batch_plans.restype = i
+            L.grav_adjoint_batch_plans.argtypes = [i, ctypes.POINTER(p), p, p, p, p]
+            L.grav_adjoint_batch_plans.restype = i
             L.grav_plan_create3d.argtypes = [i, i, i, d, d, d, u]
             L.grav_plan_create3d.restype = p
             L.grav_forward3d.argtypes = [p, p, p, p]
@@ -237,3 +243,22 @@ def grav_forward3d(plan, rho_ptr, out_ptr, stream=0) -> int:
 
 def grav_adjoint3d(plan, r_ptr, grad_ptr, stream=0) -> int:
     return _check(lib().grav_adjoint3d(plan, r_ptr, grad_ptr, stream or None))
+
+
+def _plan_array(plans):
+    arr = (ctypes.c_void_p * len(plans))()
+    for i, h in enumerate(plans):
+        arr[i] = h
+    return arr
+
+
+def grav_forward_batch_plans(plans, rho_ptr, out_ptr, ws_ptr, stream=0) -> int:
+    """One batched forward over requests on different plans of equal sizes and
+    components (request b on plans[b])."""
+    return _check(lib().grav_forward_batch_plans(len(plans), _plan_array(plans), rho_ptr, out_ptr, ws_ptr or None,
+                                                 stream or None))
+
+
+def grav_adjoint_batch_plans(plans, r_ptr, grad_ptr, ws_ptr, stream=0) -> int:
+    return _check(lib().grav_adjoint_batch_plans(len(plans), _plan_array(plans), r_ptr, grad_ptr, ws_ptr or None,
+                                                 stream or None))

@@ -274,9 +274,11 @@ inline void mark(grav_plan::TimedCall* t, int i, cudaStream_t s) {
 size_t ws_a_part(const grav_plan* p) { return round_up(p->ws_a_bytes, 256); }
 size_t ws_req_bytes(const grav_plan* p) { return ws_a_part(p) + round_up(p->ws_b_bytes, 256); }
 
+// spec_of: per-request spectra of a batched call across plans (nullptr: the
+// plan's own for every request).
 template <typename R>
 int run_forward(grav_plan* p, const void* rho, void* out, void* wa, void* wb, int batch, size_t ws_stride,
-                cudaStream_t s) {
+                cudaStream_t s, const void* const* spec_of = nullptr) {
     using C = typename cplx_of<R>::type;
     const size_t cs = ws_stride / sizeof(C);  // workspace stride in complex elements
     cudaError_t e;
@@ -288,6 +290,10 @@ int run_forward(grav_plan* p, const void* rho, void* out, void* wa, void* wb, in
     mark(tc, 1, s);
     ColumnArgs a{p->ny, p->ny_pad, p->nz, p->ncomp, p->kx_count, p->jp, p->imag_mask, p->oddv_mask,
                  p->log_t - (p->log_py - 1), p->log_t - p->log_py};
+    if (spec_of) {
+        a.spec_count = batch;
+        for (int i = 0; i < batch; ++i) a.spec_of[i] = spec_of[i];
+    }
     e = launch_forward_columns<R>(p->log_py - 1, a, wa, (const R*)p->spec, wb, p->tw, p->err_flag, s,
                                   Batch{batch, cs, cs});
     if (e != cudaSuccess) return cuda_fail(e, "forward column stage");
@@ -303,7 +309,7 @@ int run_forward(grav_plan* p, const void* rho, void* out, void* wa, void* wb, in
 
 template <typename R>
 int run_adjoint(grav_plan* p, const void* r, void* grad, void* wa, void* wb, int batch, size_t ws_stride,
-                cudaStream_t s) {
+                cudaStream_t s, const void* const* spec_of = nullptr) {
     using C = typename cplx_of<R>::type;
     const size_t cs = ws_stride / sizeof(C);
     cudaError_t e;
@@ -318,6 +324,10 @@ int run_adjoint(grav_plan* p, const void* r, void* grad, void* wa, void* wb, int
                  p->log_t - (p->log_py - 1), p->log_t - p->log_py};
     // FP32 2048 x 2048 plans: tile-major column output, read back by whole tiles
     if constexpr (sizeof(R) == 4) a.z_tiled = adjoint_tiled_ok(p->log_py - 1, p->log_px, p->nx, a) ? 1 : 0;
+    if (spec_of) {
+        a.spec_count = batch;
+        for (int i = 0; i < batch; ++i) a.spec_of[i] = spec_of[i];
+    }
     e = launch_adjoint_columns<R>(p->log_py - 1, a, wb, (const R*)p->spec, wa, p->tw, p->err_flag, s,
                                   Batch{batch, cs, cs});
     if (e != cudaSuccess) return cuda_fail(e, "adjoint column stage");
@@ -335,6 +345,46 @@ int run_adjoint(grav_plan* p, const void* r, void* grad, void* wa, void* wb, int
     if (e != cudaSuccess) return cuda_fail(e, "adjoint inverse row transform");
     mark(tc, 3, s);
     return GRAV_OK;
+}
+
+// Requests on different plans share a batched call when the plans agree in
+// everything but their kernel spectra: mesh sizes, components, precision
+// (hence the same circulant sizes, workspace layout and twiddles).
+bool same_shape(const grav_plan* a, const grav_plan* b) {
+    return a->kind == 0 && b->kind == 0 && a->nx == b->nx && a->ny == b->ny && a->nz == b->nz &&
+           a->comps == b->comps && a->fp64 == b->fp64 && a->device == b->device;
+}
+
+int batch_plans_call(int batch, grav_plan* const* plans, const void* in, void* out, void* ws, void* stream,
+                     bool adjoint) {
+    const char* name = adjoint ? "grav_adjoint_batch_plans" : "grav_forward_batch_plans";
+    if (!plans || !in || !out || !ws || batch < 1 || batch > kMaxSpecPlans) {
+        set_error("%s: null argument, or batch outside 1..%d", name, kMaxSpecPlans);
+        return GRAV_EINVAL;
+    }
+    const void* spec_of[kMaxSpecPlans];
+    for (int i = 0; i < batch; ++i) {
+        if (!plans[i] || !same_shape(plans[0], plans[i])) {
+            set_error("%s: plan %d is null or differs from plan 0 in mesh size, components, precision or kind",
+                      name, i);
+            return GRAV_EINVAL;
+        }
+        spec_of[i] = plans[i]->spec;
+    }
+    if (reinterpret_cast<uintptr_t>(ws) & 255) {
+        set_error("%s: workspace must be 256-byte aligned", name);
+        return GRAV_EINVAL;
+    }
+    grav_plan* p = plans[0];
+    void* wa = ws;
+    void* wb = (unsigned char*)ws + ws_a_part(p);
+    const size_t stride = ws_req_bytes(p);
+    cudaStream_t s = (cudaStream_t)stream;
+    if (adjoint)
+        return p->fp64 ? run_adjoint<double>(p, in, out, wa, wb, batch, stride, s, spec_of)
+                       : run_adjoint<float>(p, in, out, wa, wb, batch, stride, s, spec_of);
+    return p->fp64 ? run_forward<double>(p, in, out, wa, wb, batch, stride, s, spec_of)
+                   : run_forward<float>(p, in, out, wa, wb, batch, stride, s, spec_of);
 }
 
 int batch_call(grav_plan* plan, int batch, const void* in, void* out, void* ws, void* stream, bool adjoint) {
@@ -480,6 +530,16 @@ int grav_forward_batch(grav_plan* plan, int batch, const void* rho_dev, void* ou
 int grav_adjoint_batch(grav_plan* plan, int batch, const void* r_dev, void* grad_dev, void* workspace_dev,
                        void* stream) {
     return batch_call(plan, batch, r_dev, grad_dev, workspace_dev, stream, true);
+}
+
+int grav_forward_batch_plans(int batch, grav_plan* const* plans, const void* rho_dev, void* out_dev,
+                             void* workspace_dev, void* stream) {
+    return batch_plans_call(batch, plans, rho_dev, out_dev, workspace_dev, stream, false);
+}
+
+int grav_adjoint_batch_plans(int batch, grav_plan* const* plans, const void* r_dev, void* grad_dev,
+                             void* workspace_dev, void* stream) {
+    return batch_plans_call(batch, plans, r_dev, grad_dev, workspace_dev, stream, true);
 }
 
 void grav_plan_destroy(grav_plan* plan) {

@@ -73,8 +73,9 @@ __global__ void __maxnreg__(A5Shape::REGS)
     const int nz = a.nz, ny = a.ny;
     Xr += blockIdx.y * x_bstride;  // request of a batched call
     Z += blockIdx.y * z_bstride;
-    const float* Sk0 = spec + (size_t)kx * nz * S_ROW;                 // parity 0
-    const float* Sk1 = spec + (size_t)(a.kx_count + kx) * nz * S_ROW;  // parity 1
+    const float* specb = request_spec(a, spec, blockIdx.y);
+    const float* Sk0 = specb + (size_t)kx * nz * S_ROW;                 // parity 0
+    const float* Sk1 = specb + (size_t)(a.kx_count + kx) * nz * S_ROW;  // parity 1
 
     if (tid == 0) {
         for (int s = 0; s < L.dz; ++s) {

@@ -85,8 +85,9 @@ __global__ void __maxnreg__(W5Shape::REGS)
     X += blockIdx.y * x_bstride;  // request of a batched call
     Y += blockIdx.y * y_bstride;
     const C* Xk = X + (size_t)kx * nz * a.ny_pad;
-    const float* Sk0 = spec + (size_t)kx * nz * S_ROW;                   // parity 0
-    const float* Sk1 = spec + (size_t)(a.kx_count + kx) * nz * S_ROW;    // parity 1
+    const float* specb = request_spec(a, spec, blockIdx.y);
+    const float* Sk0 = specb + (size_t)kx * nz * S_ROW;                   // parity 0
+    const float* Sk1 = specb + (size_t)(a.kx_count + kx) * nz * S_ROW;    // parity 1
 
     if (tid == 0) {
         for (int s = 0; s < DX; ++s) mbar_init(&xfull[s], 1);

@@ -55,7 +55,19 @@ struct ColumnArgs {
                          // 1 = Z[r][n][y / 8][kx][8], row pair (y % 8) / 2 at 16-byte position
                          // ((y % 8) / 2 + kx / 2) % 4 of the run (ny_pad a multiple of 8;
                          // see launch_row_c2r_tiled)
+    // Batched calls across plans of equal sizes and components: request b
+    // reads the kernel spectra at spec_of[b] (spec_count > 0); with
+    // spec_count == 0 every request reads the kernel's spec argument.
+    int spec_count;
+    const void* spec_of[16];
 };
+constexpr int kMaxSpecPlans = 16;
+
+// Spectra of the request a CTA works on (batch index b).
+template <typename R>
+__device__ __forceinline__ const R* request_spec(const ColumnArgs& a, const R* spec, int b) {
+    return a.spec_count ? reinterpret_cast<const R*>(a.spec_of[b]) : spec;
+}
 
 }  // namespace grav
 

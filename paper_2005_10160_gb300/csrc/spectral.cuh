@@ -120,7 +120,7 @@ __global__ void __launch_bounds__(ColShape<LOGN>::J, ColShape<LOGN>::J <= 256 ? 
     Y += blockIdx.y * y_bstride;
     const C* Xk = X + (size_t)kx * nz * a.ny_pad;
     const size_t s_row = (size_t)a.ncomp * a.jp;
-    const R* Sk = spec + (size_t)(r * a.kx_count + kx) * nz * s_row;
+    const R* Sk = request_spec(a, spec, blockIdx.y) + (size_t)(r * a.kx_count + kx) * nz * s_row;
     auto stage_x = [&](int s) { return reinterpret_cast<const C*>(smem + (size_t)s * L.stage_bytes); };
     auto stage_s = [&](int s) { return reinterpret_cast<const R*>(smem + (size_t)s * L.stage_bytes + L.x_bytes); };
     auto issue = [&](int n) {
@@ -321,7 +321,7 @@ __global__ void __launch_bounds__(ColShape<LOGN>::NT, 1)
     const int kx = blockIdx.x, r = blockIdx.y;
     Xr += blockIdx.z * x_bstride;  // request of a batched call
     Z += blockIdx.z * z_bstride;
-    const R* sp = spec + (size_t)(r * a.kx_count + kx) * a.nz * a.ncomp * a.jp;
+    const R* sp = request_spec(a, spec, blockIdx.z) + (size_t)(r * a.kx_count + kx) * a.nz * a.ncomp * a.jp;
     const bool has_nyq = (r == 0 && lt == 0);
 
     C fold[XPT];

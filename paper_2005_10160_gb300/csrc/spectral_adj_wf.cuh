@@ -67,7 +67,7 @@ __global__ void __maxnreg__(AwShape::REGS)
     const int nz = a.nz, ny = a.ny;
     Xr += blockIdx.y * x_bstride;  // request of a batched call
     Z += blockIdx.y * z_bstride;
-    const float* Sk = spec + (size_t)(r * a.kx_count + kx) * nz * S_ROW;
+    const float* Sk = request_spec(a, spec, blockIdx.y) + (size_t)(r * a.kx_count + kx) * nz * S_ROW;
 
     if (tid == 0) {
         for (int s = 0; s < L.dz; ++s) {

@@ -85,7 +85,7 @@ __global__ void __maxnreg__(WfShape::REGS)
     X += blockIdx.y * x_bstride;  // request of a batched call
     Y += blockIdx.y * y_bstride;
     const C* Xk = X + (size_t)kx * nz * a.ny_pad;
-    const float* Sk = spec + (size_t)(r * a.kx_count + kx) * nz * S_ROW;
+    const float* Sk = request_spec(a, spec, blockIdx.y) + (size_t)(r * a.kx_count + kx) * nz * S_ROW;
 
     if (tid == 0) {
         for (int s = 0; s < DX; ++s) mbar_init(&xfull[s], 1);

@@ -100,7 +100,7 @@ __global__ void __launch_bounds__(WsShape<LOGN>::NT, 1) __maxnreg__(65536 / WsSh
     Y += blockIdx.y * y_bstride;
     const C* Xk = X + (size_t)kx * nz * a.ny_pad;
     const size_t s_row = (size_t)a.ncomp * a.jp;
-    const float* Sk = spec + (size_t)(r * a.kx_count + kx) * nz * s_row;
+    const float* Sk = request_spec(a, spec, blockIdx.y) + (size_t)(r * a.kx_count + kx) * nz * s_row;
 
     if (tid == 0) {
         for (int s = 0; s < L.dx; ++s) {

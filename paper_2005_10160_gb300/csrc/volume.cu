@@ -58,10 +58,12 @@ template <typename C> constexpr int rows_nseq(int logn) {
     const int n = 8192 >> logn;
     return n < 1 ? 1 : (n > 64 ? 64 : n);
 }
-// Columns per CTA of the z kernel: two buffers of TI sequences of Pz points.
+// Columns per CTA of the z kernel: two buffers of TI sequences of Pz points,
+// 4096 (FP32) or 2048 (FP64) points each, about 76 KB in all, so that two
+// CTAs share an SM.
 template <typename C> constexpr int z_tile(int logz) {
     const int cap = sizeof(C) == 8 ? 32 : 16;
-    const int n = (sizeof(C) == 8 ? 8192 : 4096) >> logz;
+    const int n = (sizeof(C) == 8 ? 4096 : 2048) >> logz;
     return n < 1 ? 1 : (n > cap ? cap : n);
 }
 
@@ -101,55 +103,78 @@ struct ZArgs {
 // Pass C.  Forward (ADJ = false): in = U[kx][n][py], out = W[kx][c][t][py].
 // Adjoint: in = U'[kx][c][t][py], out = W'[kx][n][py] = sum_c conj(S_c) . in_c
 // transformed back.  One CTA per kx and tile of TI columns ky0 .. ky0 + TI.
+// The FFTs run on per-pass twiddle tables in shared memory; a thread reads
+// every spectrum value it needs for one component before it uses any, so the
+// loads overlap.
 template <typename R, int LOGZ, int TI, bool ADJ>
-__global__ void __launch_bounds__(kVolThreads) vol_z_kernel(ZArgs a, const typename cplx<R>::type* __restrict__ in,
-                                                            typename cplx<R>::type* __restrict__ out,
-                                                            const R* __restrict__ spec3,
-                                                            const typename cplx<R>::type* __restrict__ tw) {
+__global__ void __launch_bounds__(kVolThreads, 2) vol_z_kernel(ZArgs a, const typename cplx<R>::type* __restrict__ in,
+                                                               typename cplx<R>::type* __restrict__ out,
+                                                               const R* __restrict__ spec3,
+                                                               const typename cplx<R>::type* __restrict__ tw) {
     using C = typename cplx<R>::type;
     constexpr int PZ = 1 << LOGZ, SSTR = seq_stride<C>(PZ), NT = kVolThreads;
+    constexpr int TOT = TI * PZ;
+    constexpr int IT = (TOT + NT - 1) / NT;  // elements a thread multiplies per component
     extern __shared__ __align__(16) unsigned char smem_raw[];
     C* F = reinterpret_cast<C*>(smem_raw);
     C* G = F + TI * SSTR;
+    C* tab = G + TI * SSTR;  // per-pass twiddles (fft_block.cuh)
     const int tid = threadIdx.x;
     const int kx = blockIdx.x, ky0 = blockIdx.y * TI;
     const int nz = a.nz, py = a.py;
 
+    build_tw_tab<C, LOGZ, NT>(tab, tw, a.tw_shift, tid);
     // column tile (TI columns of nz values, zero-padded to Pz) into buf
     auto load_tile = [&](C* buf, const C* src) {
-        for (int e = tid; e < TI * PZ; e += NT) {
+        for (int e = tid; e < TOT; e += NT) {
             const int i = e % TI, n = e / TI;
             C v = cmk<C>(0, 0);
             if (n < nz && ky0 + i < py) v = src[(size_t)n * py + ky0 + i];
             buf[i * SSTR + sidx<C>(n)] = v;
         }
     };
-    // spectrum value of slot c at (kx, ky0 + i, kz), as the real number v with
-    // S = v (real slot) or S = i v (imaginary slot)
-    auto spec_at = [&](int c, int i, int kz) -> R {
-        const int ky = ky0 + i;
-        const bool fy = ky > py / 2, fz = kz > PZ / 2;
-        const int jy = fy ? py - ky : ky, jz = fz ? PZ - kz : kz;
-        R v = spec3[(((size_t)c * a.kx_count + kx) * a.jyc + jy) * a.jzc + jz];
-        if ((fy && ((a.oddv_mask >> c) & 1u)) != (fz && ((a.oddw_mask >> c) & 1u))) v = -v;
-        return v;
+    // the spectrum values of slot c at this thread's elements e = tid + it NT
+    // (i = e / PZ, kz = e % PZ), as the real numbers v with S = v or S = i v
+    auto load_spec = [&](int c, R (&v)[IT]) {
+        const R* base = spec3 + ((size_t)c * a.kx_count + kx) * a.jyc * a.jzc;
+        const bool ov = (a.oddv_mask >> c) & 1u, ow = (a.oddw_mask >> c) & 1u;
+#pragma unroll
+        for (int it = 0; it < IT; ++it) {
+            const int e = tid + it * NT;
+            const int i = e / PZ, kz = e - i * PZ;
+            const int ky = ky0 + i;
+            R val = 0;
+            if (e < TOT && ky < py) {
+                const bool fy = ky > py / 2, fz = kz > PZ / 2;
+                const int jy = fy ? py - ky : ky, jz = fz ? PZ - kz : kz;
+                val = __ldg(base + (size_t)jy * a.jzc + jz);
+                if ((fy && ov) != (fz && ow)) val = -val;
+            }
+            v[it] = val;
+        }
     };
 
     if constexpr (!ADJ) {
         load_tile(F, in + (size_t)kx * nz * py);
-        __syncthreads();
-        block_fft<C, LOGZ, TI, NT, false>(F, SSTR, tw, a.tw_shift, tid);
+        __syncthreads();  // the tile and the twiddle table are in place
+        block_fft_tab<C, LOGZ, TI, NT, false>(F, SSTR, tab, tid);
+        R v[IT];
+        load_spec(0, v);
         for (int c = 0; c < a.ncomp; ++c) {
             const bool imag = (a.imag3_mask >> c) & 1u;
-            for (int e = tid; e < TI * PZ; e += NT) {
-                const int i = e / PZ, kz = e - i * PZ;
-                if (ky0 + i >= py) continue;
-                const R v = spec_at(c, i, kz);
-                const C f = F[i * SSTR + sidx<C>(kz)];
-                G[i * SSTR + sidx<C>(kz)] = imag ? cmk<C>(-v * f.y, v * f.x) : cmk<C>(v * f.x, v * f.y);
+#pragma unroll
+            for (int it = 0; it < IT; ++it) {
+                const int e = tid + it * NT;
+                if (e < TOT) {
+                    const int i = e / PZ, kz = e - i * PZ;
+                    const C f = F[i * SSTR + sidx<C>(kz)];
+                    G[i * SSTR + sidx<C>(kz)] = imag ? cmk<C>(-v[it] * f.y, v[it] * f.x)
+                                                     : cmk<C>(v[it] * f.x, v[it] * f.y);
+                }
             }
-            __syncthreads();
-            block_fft<C, LOGZ, TI, NT, true>(G, SSTR, tw, a.tw_shift, tid);
+            if (c + 1 < a.ncomp) load_spec(c + 1, v);  // in flight during the transform
+            __syncthreads();  // every product is in G
+            block_fft_tab<C, LOGZ, TI, NT, true>(G, SSTR, tab, tid);
             C* dst = out + (((size_t)kx * a.ncomp + c) * nz) * py + ky0;
             for (int e = tid; e < TI * nz; e += NT) {
                 const int i = e % TI, t = e / TI;
@@ -158,27 +183,39 @@ __global__ void __launch_bounds__(kVolThreads) vol_z_kernel(ZArgs a, const typen
             __syncthreads();  // G is rewritten by the next component
         }
     } else {
-        for (int e = tid; e < TI * PZ; e += NT) {
-            const int i = e / PZ, kz = e - i * PZ;
-            G[i * SSTR + sidx<C>(kz)] = cmk<C>(0, 0);
-        }
+        C g[IT];
+#pragma unroll
+        for (int it = 0; it < IT; ++it) g[it] = cmk<C>(0, 0);
+        R v[IT];
         for (int c = 0; c < a.ncomp; ++c) {
             load_tile(F, in + (((size_t)kx * a.ncomp + c) * nz) * py);
-            __syncthreads();
-            block_fft<C, LOGZ, TI, NT, false>(F, SSTR, tw, a.tw_shift, tid);
+            load_spec(c, v);  // in flight during the transform
+            __syncthreads();  // the tile (and, the first time, the twiddle table) is in place
+            block_fft_tab<C, LOGZ, TI, NT, false>(F, SSTR, tab, tid);
             const bool imag = (a.imag3_mask >> c) & 1u;
-            for (int e = tid; e < TI * PZ; e += NT) {
-                const int i = e / PZ, kz = e - i * PZ;
-                if (ky0 + i >= py) continue;
-                const R v = spec_at(c, i, kz);
-                const C f = F[i * SSTR + sidx<C>(kz)];
-                C& g = G[i * SSTR + sidx<C>(kz)];
-                // conj(S) f: S = v or S = i v
-                g = imag ? cmk<C>(g.x + v * f.y, g.y - v * f.x) : cmk<C>(g.x + v * f.x, g.y + v * f.y);
+#pragma unroll
+            for (int it = 0; it < IT; ++it) {
+                const int e = tid + it * NT;
+                if (e < TOT) {
+                    const int i = e / PZ, kz = e - i * PZ;
+                    const C f = F[i * SSTR + sidx<C>(kz)];
+                    // conj(S) f: S = v or S = i v
+                    g[it] = imag ? cmk<C>(g[it].x + v[it] * f.y, g[it].y - v[it] * f.x)
+                                 : cmk<C>(g[it].x + v[it] * f.x, g[it].y + v[it] * f.y);
+                }
             }
             __syncthreads();  // F is reloaded for the next component
         }
-        block_fft<C, LOGZ, TI, NT, true>(G, SSTR, tw, a.tw_shift, tid);
+#pragma unroll
+        for (int it = 0; it < IT; ++it) {
+            const int e = tid + it * NT;
+            if (e < TOT) {
+                const int i = e / PZ, kz = e - i * PZ;
+                G[i * SSTR + sidx<C>(kz)] = g[it];
+            }
+        }
+        __syncthreads();
+        block_fft_tab<C, LOGZ, TI, NT, true>(G, SSTR, tab, tid);
         C* dst = out + (size_t)kx * nz * py + ky0;
         for (int e = tid; e < TI * nz; e += NT) {
             const int i = e % TI, n = e / TI;
@@ -286,7 +323,7 @@ cudaError_t z_launch(const ZArgs& a, const void* in, void* out, const R* spec3, 
     using C = typename cplx<R>::type;
     constexpr int TI = z_tile<C>(LOGZ);
     constexpr auto k = vol_z_kernel<R, LOGZ, TI, ADJ>;
-    const size_t smem = (size_t)2 * TI * seq_stride<C>(1 << LOGZ) * sizeof(C);
+    const size_t smem = ((size_t)2 * TI * seq_stride<C>(1 << LOGZ) + tw_tab_len(LOGZ)) * sizeof(C);
     cudaError_t e = ensure_smem_limit<k>();
     if (e != cudaSuccess) return e;
     k<<<dim3(a.kx_count, (a.py + TI - 1) / TI), kVolThreads, smem, s>>>(a, (const C*)in, (C*)out, spec3,

@@ -221,3 +221,80 @@ def test_host_pipeline_matches_plain_calls(gravlib):
         for rh, oh in zip(rhos, outs):
             ref = plan.forward(rh.cuda()).cpu()
             assert torch.equal(oh, ref)
+
+
+@pytest.mark.parametrize("mesh,comps,fp64", [
+    (W.Mesh(96, 40, 8, 25.0, 20.0, 10.0, 5.0), capi.GRAV_ALL6, False),      # generic column kernels
+    (W.Mesh(6, 600, 10, 20.0, 20.0, 10.0, 5.0), capi.GRAV_ALL6, False),     # 2048-point warp columns
+    (W.Mesh(12, 300, 7, 20.0, 20.0, 10.0, 5.0), capi.GRAV_ALL6, False),     # 1024-point columns, 2 per warp
+    (W.Mesh(12, 300, 7, 20.0, 20.0, 10.0, 5.0), 0x1BF, False),              # 8 components: the fallback kernel
+    (W.Mesh(520, 528, 3, 20.0, 20.0, 10.0, 5.0), capi.GRAV_ALL6, False),    # 2048-point rows, tiled adjoint
+    (W.Mesh(37, 29, 5, 20.0, 20.0, 15.0, 4.0), capi.GRAV_ALL6, True),       # FP64
+])
+def test_batch_across_plans_matches_single_calls(gravlib, mesh, comps, fp64):
+    """grav_forward_batch_plans / grav_adjoint_batch_plans over three plans of
+    one mesh size (station heights 5, 20 and 60 m, the last with larger
+    cells): every request equals, bit for bit, the plain call on its own
+    plan."""
+    rng = np.random.default_rng(21)
+    nx, ny, nz = mesh.nx, mesh.ny, mesh.nz
+    meshes = [mesh, W.Mesh(nx, ny, nz, mesh.dx, mesh.dy, mesh.dz, 20.0),
+              W.Mesh(nx, ny, nz, 2 * mesh.dx, mesh.dy, 1.5 * mesh.dz, 60.0)]
+    plans = [Plan(m, comps, fp64=fp64) for m in meshes]
+    dt = torch.float64 if fp64 else torch.float32
+    try:
+        B = len(plans)
+        nc = plans[0].ncomp
+        ws = torch.empty(B * capi.grav_workspace_bytes(plans[0].handle) + 256, dtype=torch.uint8, device="cuda")
+        ws_ptr = (ws.data_ptr() + 255) // 256 * 256
+        x = torch.as_tensor(rng.uniform(-300, 300, (B, nz, ny, nx)), dtype=dt).cuda()
+        y = torch.empty((B, nc, ny, nx), dtype=dt, device="cuda")
+        capi.grav_forward_batch_plans([p.handle for p in plans], x.data_ptr(), y.data_ptr(), ws_ptr,
+                                      torch.cuda.current_stream().cuda_stream)
+        r = torch.as_tensor(rng.normal(size=(B, nc, ny, nx)), dtype=dt).cuda()
+        g = torch.empty((B, nz, ny, nx), dtype=dt, device="cuda")
+        capi.grav_adjoint_batch_plans([p.handle for p in plans], r.data_ptr(), g.data_ptr(), ws_ptr,
+                                      torch.cuda.current_stream().cuda_stream)
+        for i, p in enumerate(plans):
+            assert torch.equal(y[i], p.forward(x[i].contiguous())), i
+            assert torch.equal(g[i], p.adjoint(r[i].contiguous())), i
+        # plans that differ in more than their spectra are refused
+        with Plan(W.Mesh(nx, ny, nz + 1, mesh.dx, mesh.dy, mesh.dz, 5.0), comps, fp64=fp64) as other:
+            with pytest.raises(capi.GravError):
+                capi.grav_forward_batch_plans([plans[0].handle, other.handle], x.data_ptr(), y.data_ptr(), ws_ptr,
+                                              torch.cuda.current_stream().cuda_stream)
+    finally:
+        for p in plans:
+            p.close()
+
+
+def test_server_batches_requests_across_plans_of_one_size(gravlib, orc):
+    """Forward and adjoint requests on one 128 x 128 x 32 model seen from two
+    heights (10 m and 50 m): queued together they run as cross-plan batches;
+    each result equals the request run alone and matches the CPU oracle at
+    sampled stations or cells."""
+    low = W.Mesh(128, 128, 32, 20.0, 20.0, 20.0, 10.0)
+    high = W.Mesh(128, 128, 32, 20.0, 20.0, 20.0, 50.0)
+    rng = np.random.default_rng(31)
+    items = []
+    for i in range(8):
+        m = low if i % 2 == 0 else high
+        items.append(("forward", m, torch.as_tensor(W.serving_density(m, rng), dtype=torch.float32)))
+        items.append(("adjoint", m, torch.as_tensor(rng.normal(size=(6, m.ny, m.nx)), dtype=torch.float32)))
+    srv = Server(hbm_budget=8 << 30, slots=2, max_batch=8)
+    try:
+        for m in (low, high):  # plans first
+            srv.submit("forward", m, torch.zeros((m.nz, m.ny, m.nx))).wait(120)
+        with srv.lock:
+            reqs = [srv.submit(kind, m, d.cuda()) for kind, m, d in items]
+        srv.drain()
+        outs = [r.wait(60).cpu() for r in reqs]
+        stats = srv.stats()
+    finally:
+        srv.close()
+    assert stats["cross_plan_batches"] >= 2, stats
+    srng = np.random.default_rng(32)
+    for (kind, m, d), got in zip(items, outs):
+        assert torch.equal(got, _alone(kind, m, d)), (kind, m)
+        err = _oracle_sample(orc, kind, m, d, got, srng)
+        assert np.all(err <= 2e-5), (kind, m, err)

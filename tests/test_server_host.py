@@ -19,6 +19,7 @@ from paper_2005_10160_gb300 import capi, server as S
 MESH_A = (16, 16, 4, 10.0, 10.0, 10.0, 1.0)
 MESH_B = (32, 16, 4, 10.0, 10.0, 10.0, 1.0)
 MESH_C = (64, 64, 8, 10.0, 10.0, 10.0, 1.0)
+MESH_A_HIGH = (16, 16, 4, 10.0, 10.0, 10.0, 50.0)  # MESH_A seen from 50 m: same shape class
 
 
 class FakePlan:
@@ -38,7 +39,7 @@ class FakeSlot:
 
 
 class HostServer(S.Server):
-    PLAN_BYTES = {MESH_A: 1000, MESH_B: 2000, MESH_C: 5000}
+    PLAN_BYTES = {MESH_A: 1000, MESH_B: 2000, MESH_C: 5000, MESH_A_HIGH: 1000}
 
     def __init__(self, budget, slots=2, max_batch=8, graph_bytes_limit=1 << 20, req_bytes=(100, 50, 10)):
         self.budget, self.max_batch = budget, max_batch
@@ -52,6 +53,7 @@ class HostServer(S.Server):
         self.ids = itertools.count()
         self.completed, self.batches_run, self.graph_replays = [], 0, 0
         self.max_busy_slots, self.device_intervals = 0, []
+        self.building, self.cross_plan, self.plans_built = {}, True, 0
         self.device = torch.device("cpu")
         self.req_bytes = req_bytes
         self.launched = []
@@ -201,3 +203,74 @@ def test_device_overlap_counts_intervals_that_share_an_instant():
     assert srv.max_concurrent_on_device() == 1
     srv.device_intervals = []
     assert srv.max_concurrent_on_device() == 0
+
+
+def test_requests_on_plans_of_one_shape_class_share_a_batch():
+    """A later request of the same kind on another resident plan with the
+    same mesh size, components and precision joins the batch; one on a plan
+    not yet resident, or of another size, does not."""
+    srv = HostServer(budget=1 << 20, max_batch=8)
+    srv._plan(key(MESH_A))
+    srv._plan(key(MESH_A_HIGH))
+    reqs = enqueue(srv, [(MESH_A, "forward"), (MESH_A_HIGH, "forward"), (MESH_B, "forward"),
+                         (MESH_A_HIGH, "adjoint"), (MESH_A, "forward")])
+    assert [r.rid for r in srv._take_batch()] == [reqs[0].rid, reqs[1].rid, reqs[4].rid]
+    srv.cross_plan = False
+    assert [r.rid for r in srv._take_batch()] == [reqs[0].rid, reqs[4].rid]
+    srv.cross_plan = True
+    srv.plans.pop(key(MESH_A_HIGH))
+    assert [r.rid for r in srv._take_batch()] == [reqs[0].rid, reqs[4].rid]
+
+
+def test_cross_plan_batch_holds_every_plan_it_uses_and_runs_eagerly():
+    srv = HostServer(budget=1 << 20)
+    srv._plan(key(MESH_A))
+    srv._plan(key(MESH_A_HIGH))
+    reqs = enqueue(srv, [(MESH_A, "forward"), (MESH_A_HIGH, "forward")])
+    assert srv._admit(srv.slots[0])
+    assert srv.launched == [(key(MESH_A), "forward", [reqs[0].rid, reqs[1].rid], False)]
+    assert srv.plan_users[key(MESH_A)] == 1 and srv.plan_users[key(MESH_A_HIGH)] == 1
+    srv._finish(srv.slots[0])
+    assert srv.plan_users[key(MESH_A)] == 0 and srv.plan_users[key(MESH_A_HIGH)] == 0
+
+
+class AsyncHostServer(HostServer):
+    """The host server with a builder: plan builds are queued, not run."""
+
+    def __init__(self, *a, **k):
+        super().__init__(*a, **k)
+        self._builder = object()
+        self._build_q = __import__("queue").Queue()
+
+
+def test_a_plan_being_built_does_not_hold_up_requests_on_resident_plans():
+    srv = AsyncHostServer(budget=1 << 20)
+    srv.plans[key(MESH_B)] = FakePlan(MESH_B, capi.GRAV_ALL6)
+    srv.used = 2000
+    reqs = enqueue(srv, [(MESH_A, "forward"), (MESH_B, "forward")])
+    assert srv._admit(srv.slots[0])
+    assert key(MESH_A) in srv.building and srv._build_q.get_nowait() == key(MESH_A)
+    assert srv.used == 2000 + 1000 + 160  # B, A's reservation, B's batch
+    assert srv.launched == [(key(MESH_B), "forward", [reqs[1].rid], True)]
+    assert list(srv.queue) == [reqs[0]]  # waits for its plan
+    assert srv._admit(srv.slots[1]) is False  # still building
+    srv._build_done(key(MESH_A), FakePlan(MESH_A, capi.GRAV_ALL6), None)
+    assert key(MESH_A) not in srv.building and srv.plans_built == 1
+    assert srv._admit(srv.slots[1])
+    assert srv.launched[-1] == (key(MESH_A), "forward", [reqs[0].rid], True)
+
+
+def test_a_failed_build_fails_its_requests_and_returns_the_reservation():
+    srv = AsyncHostServer(budget=1 << 20)
+    reqs = enqueue(srv, [(MESH_A, "forward"), (MESH_A, "adjoint")])
+    assert srv._admit(srv.slots[0]) is False and srv.used == 1000
+    srv._build_done(key(MESH_A), None, "GravError: no memory")
+    assert srv.used == 0 and not srv.queue
+    assert all(r.done.is_set() and r.error == "GravError: no memory" for r in reqs)
+
+
+def test_a_plan_beyond_the_budget_waits_while_another_is_being_built():
+    srv = AsyncHostServer(budget=2500)
+    enqueue(srv, [(MESH_A, "forward"), (MESH_B, "forward")])
+    assert srv._admit(srv.slots[0]) is False  # A building (1000), B needs 2000 more: wait
+    assert list(srv.building) == [key(MESH_A)] and len(srv.queue) == 2
