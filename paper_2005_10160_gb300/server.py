@@ -35,6 +35,7 @@ from __future__ import annotations
 import collections
 import itertools
 import queue as queue_mod
+import sys
 import threading
 import time
 from dataclasses import dataclass, field
@@ -103,12 +104,17 @@ class Server:
     requests per batched call (at most 16 when they span several plans).
     graph_bytes_limit: per-request size (input + output + workspace) below
     which single-plan batches are replayed from CUDA graphs.  cross_plan:
-    batch requests on different plans of one shape class."""
+    batch requests on different plans of one shape class.  switch_interval:
+    the interpreter's thread switch interval while the server runs (seconds;
+    None leaves it alone): a waiter thread woken by a finished batch needs the
+    interpreter lock, and at the default 5 ms a busy thread can keep it that
+    long, which shows in the latency tail."""
 
     MAX_PLANS_PER_BATCH = 16
 
     def __init__(self, hbm_budget: int, slots: int = 4, max_batch: int = 8, device=None,
-                 graph_bytes_limit: int = 64 << 20, graph_memory: int = 2 << 30, cross_plan: bool = True):
+                 graph_bytes_limit: int = 64 << 20, graph_memory: int = 2 << 30, cross_plan: bool = True,
+                 switch_interval: float | None = 2e-4):
         self.device = torch.device("cuda", torch.cuda.current_device()) if device is None else torch.device(device)
         self.budget = int(hbm_budget)
         self.max_batch = int(max_batch)
@@ -137,6 +143,10 @@ class Server:
         with torch.cuda.device(self.device):
             self._ref_event.record(torch.cuda.current_stream(self.device))
         self._stop = False
+        self._old_switch = None
+        if switch_interval is not None:
+            self._old_switch = sys.getswitchinterval()
+            sys.setswitchinterval(min(self._old_switch, float(switch_interval)))
         self._build_q: queue_mod.Queue = queue_mod.Queue()
         self._builder = threading.Thread(target=self._build_loop, name="grav-builder", daemon=True)
         self._builder.start()
@@ -189,6 +199,9 @@ class Server:
         for p in self.plans.values():
             p.close()
         self.plans.clear()
+        if self._old_switch is not None:
+            sys.setswitchinterval(self._old_switch)
+            self._old_switch = None
 
     def stats(self) -> dict:
         lat = np.array([r.latency for r in self.completed if r.error is None])
