@@ -104,7 +104,7 @@ __global__ void __maxnreg__(A5Shape::REGS)
             u[16 + n1] = tw32<false>(v, n1);  // parity 1: fold factor W_32^n1
         }
         C* fb = ring + c * FS;
-        warp_fft512x2<false>(u, fb, t2, lane);
+        warp_fft512x2<false, false>(u, fb, t2, lane);  // scalar butterflies: register cap
         const int base = (lane >> 4) * N + (lane & 15);
 #pragma unroll
         for (int j = 0; j < 32; ++j) fb[base + 16 * bitrev5(j)] = u[j];
@@ -213,7 +213,7 @@ __global__ void __maxnreg__(A5Shape::REGS)
                 u[16 + n1] = zb[N + 32 * n1 + lane];
             }
             __syncwarp();
-            warp_fft512x2<true>(u, zb, t2, lane);
+            warp_fft512x2<true, false>(u, zb, t2, lane);
             mbar_arrive(&zempty[sz]);  // this lane is done with the slot (transposes included)
             C* dst = Z + ((size_t)(h * a.kx_count + kx) * nz + n) * a.ny_pad;
             if (h) {

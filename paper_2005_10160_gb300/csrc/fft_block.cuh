@@ -27,6 +27,13 @@ template <typename C> __device__ __forceinline__ C cmul(C a, C b) {
     return cmk<C>(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
 }
 template <typename C> __device__ __forceinline__ C cconj(C a) { return cmk<C>(a.x, -a.y); }
+// FP32: one packed two-wide instruction per complex add or subtract
+// (sm_100 family); a - b as fma(b, -1, a) rounds exactly like the
+// subtraction, so results are bit for bit those of the scalar form.
+template <> __device__ __forceinline__ float2 cadd<float2>(float2 a, float2 b) { return __fadd2_rn(a, b); }
+template <> __device__ __forceinline__ float2 csub<float2>(float2 a, float2 b) {
+    return __ffma2_rn(b, make_float2(-1.f, -1.f), a);
+}
 template <typename C> __device__ __forceinline__ C cscale(C a, decltype(C::x) s) { return cmk<C>(a.x * s, a.y * s); }
 // Multiply by -i (forward sign) or +i (inverse sign).
 template <typename C, bool INV> __device__ __forceinline__ C cmul_ni(C a) {

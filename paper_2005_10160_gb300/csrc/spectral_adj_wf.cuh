@@ -37,7 +37,7 @@ struct AwShape {
 
 struct AwSmem {
     int dz;
-    uint32_t slot_off, tw_off, t2_off, bar_off, flag_off, total;
+    uint32_t slot_off, tw_off, t2_off, stage_off, bar_off, flag_off, total;
 };
 
 // IM, OV: the plan's imaginary-spectrum and odd-in-y component masks when
@@ -197,26 +197,30 @@ __global__ void __maxnreg__(AwShape::REGS)
             __syncwarp();
             warp_fft1024<true>(u, zb, t2, lane);
             if (a.z_tiled) {
-                // Stage the layer in the slot in the order of its tiles, Z[.][.][y / 8][kx][8]
+                // The slot was only the transform's transpose area: free it now.  Stage the
+                // layer in this warp's own buffer in the order of its tiles, Z[.][.][y / 8][kx][8]
                 // with row pair (y % 8) / 2 at 16-byte position ((y % 8) / 2 + kx / 2) % 4,
-                // and write it with one tensor store (zmap: 8 x kx x y/8 x (r, n) x request).
+                // and write it with one tensor store (zmap: 8 x kx x y/8 x (r, n) x request)
+                // that is not waited for: the next layer waits, before it restages, until
+                // this store has read the buffer.
+                mbar_arrive(&zempty[sz]);
+                C* stg = reinterpret_cast<C*>(smem + L.stage_off) + f * N;
+                if (lane == 0) bulk_wait_read_all();  // the previous layer's store has read the buffer
+                __syncwarp();
                 const int pos = 2 * ((((lane & 7) >> 1) + (kx >> 1)) & 3) + (lane & 1);  // y % 8 = lane % 8
 #pragma unroll
                 for (int j = 0; j < 32; ++j) {
                     const int y = lane + 32 * bitrev5(j);
                     C v = u[j];
                     if (r) v = cmul(v, cconj(tws[y]));
-                    zb[(y & ~7) + pos] = v;
+                    stg[(y & ~7) + pos] = v;
                 }
                 fence_proxy_async_smem();  // these writes before the tensor store's reads
                 __syncwarp();
                 if (lane == 0) {
-                    tma_store_5d(&zmap, zb, 0, kx, 0, r * nz + n, blockIdx.y);
+                    tma_store_5d(&zmap, stg, 0, kx, 0, r * nz + n, blockIdx.y);
                     bulk_commit();
-                    bulk_wait_read_all();  // the slot has been read: it may be refilled
                 }
-                __syncwarp();
-                mbar_arrive(&zempty[sz]);
             } else {
                 mbar_arrive(&zempty[sz]);  // this lane is done with the slot (transposes included)
                 C* dst = Z + ((size_t)(r * a.kx_count + kx) * nz + n) * a.ny_pad;
@@ -245,7 +249,8 @@ inline AwSmem aw_smem(int ny_pad, int ncomp, int jp, int nc_inst, int max_bytes)
         l.slot_off = 0;
         l.tw_off = (uint32_t)(dz * AwShape::SLOT * sizeof(float2));
         l.t2_off = l.tw_off + AwShape::N * sizeof(float2);
-        l.bar_off = l.t2_off + AwShape::N * sizeof(float2);
+        l.stage_off = (l.t2_off + AwShape::N * sizeof(float2) + 127) & ~127u;  // tensor-store sources: 128-byte aligned
+        l.bar_off = l.stage_off + AwShape::FWARPS * AwShape::N * sizeof(float2);
         l.flag_off = l.bar_off + 2 * dz * 8;
         l.total = l.flag_off + 16;
         if ((int)l.total <= max_bytes) return l;

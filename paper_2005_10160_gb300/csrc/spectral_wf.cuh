@@ -163,7 +163,7 @@ __global__ void __maxnreg__(WfShape::REGS)
                 for (int n1 = 0; n1 < 32; ++n1) u[n1] = tw64(u[n1], n1);  // fold factor W_64^n1
             }
             C* fb = fring + sf * FS;
-            warp_fft1024<false>(u, fb, t2, lane);
+            warp_fft1024<false, false>(u, fb, t2, lane);  // scalar butterflies: 80 registers
 #pragma unroll
             for (int j = 0; j < 32; ++j) fb[lane + 32 * bitrev5(j)] = u[j];
             if (lane < NC) fb[N + lane] = make_float2(snyq, 0.f);
@@ -189,7 +189,7 @@ __global__ void __maxnreg__(WfShape::REGS)
 #pragma unroll
                 for (int n1 = 0; n1 < 32; ++n1) u[n1] = cmul(u[n1], w);
             }
-            warp_fft1024<true>(u, fb, t2, lane);
+            warp_fft1024<true, false>(u, fb, t2, lane);
             C* dst = Y + ((size_t)(r * a.kx_count + kx) * a.ncomp + c) * a.ny_pad;
             if (r) {
                 // unfold: W_2048^-y with y = lane + 32 k is W_2048^-lane W_64^-k

@@ -37,6 +37,7 @@
 // The adjoint runs the same passes from r[c][t][y][x], multiplies by the
 // conjugate spectra and sums over components in pass C (the transpose).
 #include <new>
+#include <type_traits>
 
 #include "fft_block.cuh"
 #include "grav_internal.h"
@@ -65,6 +66,24 @@ template <typename C> constexpr int z_tile(int logz) {
     const int cap = sizeof(C) == 8 ? 32 : 16;
     const int n = (sizeof(C) == 8 ? 4096 : 2048) >> logz;
     return n < 1 ? 1 : (n > cap ? cap : n);
+}
+
+// Columns per warp of the z kernel: an eighth of the tile, and at least
+// enough that every lane owns an element (Pz < 32); warps = TI / columns.
+constexpr int z_cols_per_warp(int ti, int logz) {
+    const int by_warps = ti / 8 > 1 ? ti / 8 : 1;
+    const int by_lanes = (32 + (1 << logz) - 1) >> logz;
+    const int c = by_warps > by_lanes ? by_warps : by_lanes;
+    return c < ti ? c : ti;
+}
+// Whether each warp transforms its own columns (a lane then holds at most 16
+// FP32 or 8 FP64 values of them) or, for long columns, the whole CTA of 256
+// threads transforms the tile together.
+constexpr bool z_warp_mode(int ti, int logz, bool fp64) {
+    return z_cols_per_warp(ti, logz) * (1 << logz) / 32 <= (fp64 ? 8 : 16);
+}
+constexpr int z_threads(int ti, int logz, bool fp64) {
+    return z_warp_mode(ti, logz, fp64) ? 32 * (ti / z_cols_per_warp(ti, logz)) : 256;
 }
 
 // ---------------------------------------------------------------------------
@@ -103,48 +122,69 @@ struct ZArgs {
 // Pass C.  Forward (ADJ = false): in = U[kx][n][py], out = W[kx][c][t][py].
 // Adjoint: in = U'[kx][c][t][py], out = W'[kx][n][py] = sum_c conj(S_c) . in_c
 // transformed back.  One CTA per kx and tile of TI columns ky0 .. ky0 + TI.
-// The FFTs run on per-pass twiddle tables in shared memory; a thread reads
-// every spectrum value it needs for one component before it uses any, so the
-// loads overlap.
+// The tile is loaded and stored by the whole CTA (rows of TI consecutive
+// columns, coalesced); in between each warp transforms, multiplies and
+// transforms back its own SPW columns with warp-level syncs only, on per-pass
+// twiddle tables in shared memory.  A lane reads every spectrum value it needs
+// for one component before it uses any, so those loads overlap.
+struct WarpSync {
+    __device__ __forceinline__ void operator()() const { __syncwarp(); }
+};
+
 template <typename R, int LOGZ, int TI, bool ADJ>
-__global__ void __launch_bounds__(kVolThreads, 2) vol_z_kernel(ZArgs a, const typename cplx<R>::type* __restrict__ in,
-                                                               typename cplx<R>::type* __restrict__ out,
-                                                               const R* __restrict__ spec3,
-                                                               const typename cplx<R>::type* __restrict__ tw) {
+__global__ void __launch_bounds__(z_threads(TI, LOGZ, sizeof(R) == 8), 2)
+    vol_z_kernel(ZArgs a, const typename cplx<R>::type* __restrict__ in, typename cplx<R>::type* __restrict__ out,
+                 const R* __restrict__ spec3, const typename cplx<R>::type* __restrict__ tw) {
     using C = typename cplx<R>::type;
-    constexpr int PZ = 1 << LOGZ, SSTR = seq_stride<C>(PZ), NT = kVolThreads;
-    constexpr int TOT = TI * PZ;
-    constexpr int IT = (TOT + NT - 1) / NT;  // elements a thread multiplies per component
+    constexpr int PZ = 1 << LOGZ, SSTR = seq_stride<C>(PZ);
+    constexpr bool WARP = z_warp_mode(TI, LOGZ, sizeof(R) == 8);
+    constexpr int NT = z_threads(TI, LOGZ, sizeof(R) == 8);
+    // a group transforms its columns together: one warp (WARP) or the CTA
+    constexpr int GT = WARP ? 32 : NT;                                // threads of a group
+    constexpr int GC = WARP ? z_cols_per_warp(TI, LOGZ) : TI;         // columns of a group
+    constexpr int IT = GC * PZ / GT;  // elements a thread multiplies per component
+    using Sync = typename std::conditional<WARP, WarpSync, BlockSync>::type;
+    static_assert(GC * PZ % GT == 0 && IT > 0, "whole elements per thread");
     extern __shared__ __align__(16) unsigned char smem_raw[];
     C* F = reinterpret_cast<C*>(smem_raw);
     C* G = F + TI * SSTR;
     C* tab = G + TI * SSTR;  // per-pass twiddles (fft_block.cuh)
     const int tid = threadIdx.x;
+    const int grp = WARP ? tid >> 5 : 0, gtid = WARP ? (tid & 31) : tid;
     const int kx = blockIdx.x, ky0 = blockIdx.y * TI;
     const int nz = a.nz, py = a.py;
+    C* Fw = F + grp * GC * SSTR;  // this group's columns
+    C* Gw = G + grp * GC * SSTR;
 
     build_tw_tab<C, LOGZ, NT>(tab, tw, a.tw_shift, tid);
     // column tile (TI columns of nz values, zero-padded to Pz) into buf
     auto load_tile = [&](C* buf, const C* src) {
-        for (int e = tid; e < TOT; e += NT) {
+        for (int e = tid; e < TI * PZ; e += NT) {
             const int i = e % TI, n = e / TI;
             C v = cmk<C>(0, 0);
             if (n < nz && ky0 + i < py) v = src[(size_t)n * py + ky0 + i];
             buf[i * SSTR + sidx<C>(n)] = v;
         }
     };
-    // the spectrum values of slot c at this thread's elements e = tid + it NT
-    // (i = e / PZ, kz = e % PZ), as the real numbers v with S = v or S = i v
+    auto store_tile = [&](const C* buf, C* dst) {
+        for (int e = tid; e < TI * nz; e += NT) {
+            const int i = e % TI, t = e / TI;
+            if (ky0 + i < py) dst[(size_t)t * py + i] = buf[i * SSTR + sidx<C>(t)];
+        }
+    };
+    // the spectrum values of slot c at this thread's elements e = gtid + GT it
+    // of its group's columns (i = e / PZ, kz = e % PZ), as the real numbers v
+    // with S = v or S = i v
     auto load_spec = [&](int c, R (&v)[IT]) {
         const R* base = spec3 + ((size_t)c * a.kx_count + kx) * a.jyc * a.jzc;
         const bool ov = (a.oddv_mask >> c) & 1u, ow = (a.oddw_mask >> c) & 1u;
 #pragma unroll
         for (int it = 0; it < IT; ++it) {
-            const int e = tid + it * NT;
+            const int e = gtid + GT * it;
             const int i = e / PZ, kz = e - i * PZ;
-            const int ky = ky0 + i;
+            const int ky = ky0 + grp * GC + i;
             R val = 0;
-            if (e < TOT && ky < py) {
+            if (ky < py) {
                 const bool fy = ky > py / 2, fz = kz > PZ / 2;
                 const int jy = fy ? py - ky : ky, jz = fz ? PZ - kz : kz;
                 val = __ldg(base + (size_t)jy * a.jzc + jz);
@@ -157,29 +197,24 @@ __global__ void __launch_bounds__(kVolThreads, 2) vol_z_kernel(ZArgs a, const ty
     if constexpr (!ADJ) {
         load_tile(F, in + (size_t)kx * nz * py);
         __syncthreads();  // the tile and the twiddle table are in place
-        block_fft_tab<C, LOGZ, TI, NT, false>(F, SSTR, tab, tid);
+        block_fft_tab<C, LOGZ, GC, GT, false>(Fw, SSTR, tab, gtid, Sync{});
         R v[IT];
         load_spec(0, v);
         for (int c = 0; c < a.ncomp; ++c) {
             const bool imag = (a.imag3_mask >> c) & 1u;
 #pragma unroll
             for (int it = 0; it < IT; ++it) {
-                const int e = tid + it * NT;
-                if (e < TOT) {
-                    const int i = e / PZ, kz = e - i * PZ;
-                    const C f = F[i * SSTR + sidx<C>(kz)];
-                    G[i * SSTR + sidx<C>(kz)] = imag ? cmk<C>(-v[it] * f.y, v[it] * f.x)
-                                                     : cmk<C>(v[it] * f.x, v[it] * f.y);
-                }
+                const int e = gtid + GT * it;
+                const int i = e / PZ, kz = e - i * PZ;
+                const C f = Fw[i * SSTR + sidx<C>(kz)];
+                Gw[i * SSTR + sidx<C>(kz)] = imag ? cmk<C>(-v[it] * f.y, v[it] * f.x)
+                                                  : cmk<C>(v[it] * f.x, v[it] * f.y);
             }
             if (c + 1 < a.ncomp) load_spec(c + 1, v);  // in flight during the transform
-            __syncthreads();  // every product is in G
-            block_fft_tab<C, LOGZ, TI, NT, true>(G, SSTR, tab, tid);
-            C* dst = out + (((size_t)kx * a.ncomp + c) * nz) * py + ky0;
-            for (int e = tid; e < TI * nz; e += NT) {
-                const int i = e % TI, t = e / TI;
-                if (ky0 + i < py) dst[(size_t)t * py + i] = G[i * SSTR + sidx<C>(t)];
-            }
+            Sync{}();  // the group's products are in G
+            block_fft_tab<C, LOGZ, GC, GT, true>(Gw, SSTR, tab, gtid, Sync{});
+            __syncthreads();  // every warp's columns are transformed back
+            store_tile(G, out + (((size_t)kx * a.ncomp + c) * nz) * py + ky0);
             __syncthreads();  // G is rewritten by the next component
         }
     } else {
@@ -191,36 +226,29 @@ __global__ void __launch_bounds__(kVolThreads, 2) vol_z_kernel(ZArgs a, const ty
             load_tile(F, in + (((size_t)kx * a.ncomp + c) * nz) * py);
             load_spec(c, v);  // in flight during the transform
             __syncthreads();  // the tile (and, the first time, the twiddle table) is in place
-            block_fft_tab<C, LOGZ, TI, NT, false>(F, SSTR, tab, tid);
+            block_fft_tab<C, LOGZ, GC, GT, false>(Fw, SSTR, tab, gtid, Sync{});
             const bool imag = (a.imag3_mask >> c) & 1u;
 #pragma unroll
             for (int it = 0; it < IT; ++it) {
-                const int e = tid + it * NT;
-                if (e < TOT) {
-                    const int i = e / PZ, kz = e - i * PZ;
-                    const C f = F[i * SSTR + sidx<C>(kz)];
-                    // conj(S) f: S = v or S = i v
-                    g[it] = imag ? cmk<C>(g[it].x + v[it] * f.y, g[it].y - v[it] * f.x)
-                                 : cmk<C>(g[it].x + v[it] * f.x, g[it].y + v[it] * f.y);
-                }
+                const int e = gtid + GT * it;
+                const int i = e / PZ, kz = e - i * PZ;
+                const C f = Fw[i * SSTR + sidx<C>(kz)];
+                // conj(S) f: S = v or S = i v
+                g[it] = imag ? cmk<C>(g[it].x + v[it] * f.y, g[it].y - v[it] * f.x)
+                             : cmk<C>(g[it].x + v[it] * f.x, g[it].y + v[it] * f.y);
             }
             __syncthreads();  // F is reloaded for the next component
         }
 #pragma unroll
         for (int it = 0; it < IT; ++it) {
-            const int e = tid + it * NT;
-            if (e < TOT) {
-                const int i = e / PZ, kz = e - i * PZ;
-                G[i * SSTR + sidx<C>(kz)] = g[it];
-            }
+            const int e = gtid + GT * it;
+            const int i = e / PZ, kz = e - i * PZ;
+            Gw[i * SSTR + sidx<C>(kz)] = g[it];
         }
+        Sync{}();
+        block_fft_tab<C, LOGZ, GC, GT, true>(Gw, SSTR, tab, gtid, Sync{});
         __syncthreads();
-        block_fft_tab<C, LOGZ, TI, NT, true>(G, SSTR, tab, tid);
-        C* dst = out + (size_t)kx * nz * py + ky0;
-        for (int e = tid; e < TI * nz; e += NT) {
-            const int i = e % TI, n = e / TI;
-            if (ky0 + i < py) dst[(size_t)n * py + i] = G[i * SSTR + sidx<C>(n)];
-        }
+        store_tile(G, out + (size_t)kx * nz * py + ky0);
     }
 }
 
@@ -322,12 +350,12 @@ template <typename R, int LOGZ, bool ADJ>
 cudaError_t z_launch(const ZArgs& a, const void* in, void* out, const R* spec3, const void* tw, cudaStream_t s) {
     using C = typename cplx<R>::type;
     constexpr int TI = z_tile<C>(LOGZ);
+    constexpr int NT = z_threads(TI, LOGZ, sizeof(R) == 8);
     constexpr auto k = vol_z_kernel<R, LOGZ, TI, ADJ>;
     const size_t smem = ((size_t)2 * TI * seq_stride<C>(1 << LOGZ) + tw_tab_len(LOGZ)) * sizeof(C);
     cudaError_t e = ensure_smem_limit<k>();
     if (e != cudaSuccess) return e;
-    k<<<dim3(a.kx_count, (a.py + TI - 1) / TI), kVolThreads, smem, s>>>(a, (const C*)in, (C*)out, spec3,
-                                                                       (const C*)tw);
+    k<<<dim3(a.kx_count, (a.py + TI - 1) / TI), NT, smem, s>>>(a, (const C*)in, (C*)out, spec3, (const C*)tw);
     return cudaGetLastError();
 }
 

@@ -82,8 +82,11 @@ __host__ __device__ constexpr int bitrev5(int j) {
 }
 
 // 32-point DFT in registers, radix-2 decimation in frequency: natural order
-// in, u[j] = X[bitrev5(j)] out.
-template <bool INV> __device__ __forceinline__ void dft32(float2 (&u)[32]) {
+// in, u[j] = X[bitrev5(j)] out.  PACKED: each complex add and subtract is
+// one two-wide FP32 instruction (same roundings as the scalar form); a
+// kernel at a tight register cap may take the scalar form, which needs no
+// aligned register pairs.
+template <bool INV, bool PACKED = true> __device__ __forceinline__ void dft32(float2 (&u)[32]) {
 #pragma unroll
     for (int h = 16; h >= 1; h >>= 1) {
 #pragma unroll
@@ -91,8 +94,15 @@ template <bool INV> __device__ __forceinline__ void dft32(float2 (&u)[32]) {
 #pragma unroll
             for (int i = 0; i < h; ++i) {
                 const float2 a = u[b + i], c = u[b + i + h];
-                u[b + i] = make_float2(a.x + c.x, a.y + c.y);
-                u[b + i + h] = tw32<INV>(make_float2(a.x - c.x, a.y - c.y), i * (16 / h));
+                const int j = i * (16 / h);
+                if constexpr (PACKED) {
+                    u[b + i] = cadd(a, c);
+                    // twiddle -1 folds into the subtraction; the others act on a - c
+                    u[b + i + h] = j == 16 ? csub(c, a) : tw32<INV>(csub(a, c), j);
+                } else {
+                    u[b + i] = make_float2(a.x + c.x, a.y + c.y);
+                    u[b + i + h] = tw32<INV>(make_float2(a.x - c.x, a.y - c.y), j);
+                }
             }
         }
     }
@@ -101,9 +111,9 @@ template <bool INV> __device__ __forceinline__ void dft32(float2 (&u)[32]) {
 // 1024-point FFT by one warp.  In: u[n1] = x[32 n1 + lane].  Out: u[j] =
 // X[lane + 32 bitrev5(j)].  tr: the warp's 32 x 33 transpose area; t2[k1 32 +
 // lane] = W_1024^(lane k1).  tr may be overwritten by the caller afterwards.
-template <bool INV>
+template <bool INV, bool PACKED = true>
 __device__ __forceinline__ void warp_fft1024(float2 (&u)[32], float2* tr, const float2* t2, int lane) {
-    dft32<INV>(u);
+    dft32<INV, PACKED>(u);
 #pragma unroll
     for (int j = 0; j < 32; ++j) {
         const int k1 = bitrev5(j);
@@ -115,7 +125,7 @@ __device__ __forceinline__ void warp_fft1024(float2 (&u)[32], float2* tr, const 
 #pragma unroll
     for (int n2 = 0; n2 < 32; ++n2) u[n2] = tr[lane * 33 + n2];
     __syncwarp();
-    dft32<INV>(u);
+    dft32<INV, PACKED>(u);
 }
 
 __host__ __device__ constexpr int bitrev4(int j) { return ((j & 1) << 3) | ((j & 2) << 1) | ((j & 4) >> 1) | ((j & 8) >> 3); }
@@ -123,7 +133,7 @@ __host__ __device__ constexpr int bitrev4(int j) { return ((j & 1) << 3) | ((j &
 // 16-point DFT of u[OFF .. OFF + 15] in registers, radix-2 decimation in
 // frequency (W_16^k = W_32^(2k)): natural order in, u[OFF + j] = X[bitrev4(j)]
 // out.
-template <bool INV, int OFF> __device__ __forceinline__ void dft16(float2 (&u)[32]) {
+template <bool INV, int OFF, bool PACKED = true> __device__ __forceinline__ void dft16(float2 (&u)[32]) {
 #pragma unroll
     for (int h = 8; h >= 1; h >>= 1) {
 #pragma unroll
@@ -131,8 +141,13 @@ template <bool INV, int OFF> __device__ __forceinline__ void dft16(float2 (&u)[3
 #pragma unroll
             for (int i = 0; i < h; ++i) {
                 const float2 a = u[OFF + b + i], c = u[OFF + b + i + h];
-                u[OFF + b + i] = make_float2(a.x + c.x, a.y + c.y);
-                u[OFF + b + i + h] = tw32<INV>(make_float2(a.x - c.x, a.y - c.y), 2 * i * (8 / h));
+                if constexpr (PACKED) {
+                    u[OFF + b + i] = cadd(a, c);
+                    u[OFF + b + i + h] = tw32<INV>(csub(a, c), 2 * i * (8 / h));
+                } else {
+                    u[OFF + b + i] = make_float2(a.x + c.x, a.y + c.y);
+                    u[OFF + b + i + h] = tw32<INV>(make_float2(a.x - c.x, a.y - c.y), 2 * i * (8 / h));
+                }
             }
         }
     }
@@ -146,10 +161,10 @@ template <bool INV, int OFF> __device__ __forceinline__ void dft16(float2 (&u)[3
 // at (k1, n2 = lane), W_512^(n2 k1) for a plain pair of transforms (a caller
 // may fold a factor constant over n1 into it).  tr: the warp's 32 x 33
 // transpose area, free for the caller afterwards.
-template <bool INV>
+template <bool INV, bool PACKED = true>
 __device__ __forceinline__ void warp_fft512x2(float2 (&u)[32], float2* tr, const float2* t2, int lane) {
-    dft16<INV, 0>(u);
-    dft16<INV, 16>(u);
+    dft16<INV, 0, PACKED>(u);
+    dft16<INV, 16, PACKED>(u);
 #pragma unroll
     for (int h = 0; h < 2; ++h) {
 #pragma unroll
@@ -164,7 +179,7 @@ __device__ __forceinline__ void warp_fft512x2(float2 (&u)[32], float2* tr, const
 #pragma unroll
     for (int n2 = 0; n2 < 32; ++n2) u[n2] = tr[lane * 33 + n2];
     __syncwarp();
-    dft32<INV>(u);
+    dft32<INV, PACKED>(u);
 }
 
 }  // namespace grav
