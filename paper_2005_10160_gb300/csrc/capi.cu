@@ -180,8 +180,10 @@ template <typename R>
 int make_spectra(grav_plan* p) {
     // FP64 staging: the embedded kernels of a chunk of layers and their row
     // transforms, bounded to about 2 GB.
-    const size_t per_layer = (size_t)p->ncomp * p->py * p->px * sizeof(double) +
-                             (size_t)p->kx_count * p->ncomp * p->py * 2 * sizeof(double);
+    // rows b < py / 2 of each embedded kernel (the other half mirrors them)
+    const int hy = p->py / 2;
+    const size_t per_layer = (size_t)p->ncomp * hy * p->px * sizeof(double) +
+                             (size_t)p->kx_count * p->ncomp * hy * 2 * sizeof(double);
     const size_t budget = (size_t)2 << 30;
     int nzc = (int)(budget / per_layer);
     if (nzc < 1) nzc = 1;
@@ -199,8 +201,8 @@ int make_spectra(grav_plan* p) {
     }
     double* E = nullptr;
     void* Ehat = nullptr;
-    const size_t e_bytes = (size_t)nzc * p->ncomp * p->py * p->px * sizeof(double);
-    const size_t eh_bytes = (size_t)p->kx_count * nzc * p->ncomp * p->py * 2 * sizeof(double);
+    const size_t e_bytes = (size_t)nzc * p->ncomp * hy * p->px * sizeof(double);
+    const size_t eh_bytes = (size_t)p->kx_count * nzc * p->ncomp * hy * 2 * sizeof(double);
     if ((rc = dev_alloc(&E, e_bytes, "kernel staging")) == GRAV_OK &&
         (rc = dev_alloc(&Ehat, eh_bytes, "kernel row-transform staging")) == GRAV_OK) {
         cudaStream_t s;
@@ -214,22 +216,23 @@ int make_spectra(grav_plan* p) {
                 const int n1 = n0 + nzc < p->nz ? n0 + nzc : p->nz;
                 const int cnt = n1 - n0;
                 const int O = cnt * p->ncomp;
-                if ((ce = cudaMemsetAsync(E, 0, (size_t)O * p->py * p->px * sizeof(double), s)) != cudaSuccess) {
+                if ((ce = cudaMemsetAsync(E, 0, (size_t)O * hy * p->px * sizeof(double), s)) != cudaSuccess) {
                     rc = cuda_fail(ce, "cudaMemsetAsync(kernel staging)");
                     break;
                 }
-                if ((ce = launch_kernel_gen(g, p->comps, n0, n1, 0, p->px, p->py, E, s)) != cudaSuccess) {
+                if ((ce = launch_kernel_gen(g, p->comps, n0, n1, 2, p->px, p->py, E, s)) != cudaSuccess) {
                     rc = cuda_fail(ce, "kernel generation launch");
                     break;
                 }
-                // rows o = slot * cnt + (n - n0) of length px, py of them per o
-                if ((ce = launch_row_r2c<double>(p->log_px, E, (size_t)p->py * p->px, (size_t)p->px, p->px, p->py, O,
-                                                 Ehat, p->py, tw64, p->log_t, s)) != cudaSuccess) {
+                // rows o = slot * cnt + (n - n0) of length px, py / 2 of them per o
+                if ((ce = launch_row_r2c<double>(p->log_px, E, (size_t)hy * p->px, (size_t)p->px, p->px, hy, O,
+                                                 Ehat, hy, tw64, p->log_t, s)) != cudaSuccess) {
                     rc = cuda_fail(ce, "kernel row transform launch");
                     break;
                 }
                 if ((ce = launch_spec_extract<R>(p->log_py - 1, Ehat, p->kx_count, cnt, p->ncomp, n0, p->nz, p->jp,
-                                                 p->imag_mask, scale, (R*)p->spec, tw64, p->log_t, s)) != cudaSuccess) {
+                                                 p->imag_mask, p->oddv_mask, scale, (R*)p->spec, tw64, p->log_t,
+                                                 s)) != cudaSuccess) {
                     rc = cuda_fail(ce, "kernel spectra launch");
                     break;
                 }

@@ -158,6 +158,9 @@ void free_plan(grav_plan* p);
 // ---- kernel generation (kernel_gen.cu) ----
 // mode 0: embed into a circulant array E[(c * nzc + n) * py + b][a] of size
 //         py x px per (component, layer); E must be zeroed beforehand.
+// mode 2: the same, rows b < py / 2 only, E[(c * nzc + n) * (py / 2) + b][a]
+//         (the embedded kernel is even or odd in y, so row py - b is row b
+//         times the component's sign, and row py / 2 is zero).
 // mode 1: dense offset grid K[c][n][2ny-1][2nx-1].
 cudaError_t launch_kernel_gen(const Geometry& g, unsigned comps, int n0, int n1, int mode,
                               int px, int py, double* out, cudaStream_t s);
@@ -228,10 +231,12 @@ template <> cudaError_t launch_adjoint_columns<float>(int, const ColumnArgs&, co
 template <> cudaError_t launch_adjoint_columns<double>(int, const ColumnArgs&, const void*, const double*, void*,
                                                       const void*, int*, cudaStream_t, Batch);
 // Column FFT of embedded kernel row transforms and extraction of the stored
-// real numbers.  Ehat[kx][o][b] (b < py, row stride py), o = c * nzc + n.
+// real numbers.  Ehat[kx][o][b] for b < py / 2 (row stride py / 2), o = c *
+// nzc + n; row py - b is row b times -1 for components odd in y (bit s of
+// oddv_mask), row py / 2 is zero.
 template <typename RO>
 cudaError_t launch_spec_extract(int log_n, const void* ehat, int kx_count, int nzc, int ncomp,
-                                int n0, int nz, int jp, unsigned imag_mask, double scale, RO* spec,
-                                const void* tw64, int log_t, cudaStream_t s);
+                                int n0, int nz, int jp, unsigned imag_mask, unsigned oddv_mask, double scale,
+                                RO* spec, const void* tw64, int log_t, cudaStream_t s);
 
 }  // namespace grav

@@ -123,6 +123,11 @@ __global__ void __launch_bounds__(kGenTX * kGenTY)
                         if (mode == 0) {
                             const int a = (px - U) & (px - 1), b = (py - V) & (py - 1);
                             idx = (((size_t)s * nzc + (n - n0)) * py + b) * px + a;
+                        } else if (mode == 2) {
+                            // rows b = -V < py / 2 only (V <= 0): the rest mirror them
+                            if (V > 0) continue;
+                            const int a = (px - U) & (px - 1), b = -V;
+                            idx = (((size_t)s * nzc + (n - n0)) * (py / 2) + b) * px + a;
                         } else {
                             idx = (((size_t)s * g.nz + n) * wy + (V + g.ny - 1)) * wx + (U + g.nx - 1);
                         }
