@@ -274,6 +274,7 @@ constexpr size_t kCtT2Off = kCtAreaOff + (size_t)kCtRows * kWarpFftSlot * sizeof
 constexpr size_t kCtBarOff = kCtT2Off + 1024 * sizeof(float2);
 constexpr size_t kCtSmem = kCtBarOff + 16;
 
+template <bool TWO>
 __global__ void __launch_bounds__(kCtThreads, 1)
     row_c2r_tiled_kernel(const float2* __restrict__ in0, const float2* __restrict__ in1, int ny, int nz,
                          float* __restrict__ out, size_t out_stride, int l_out, const float2* __restrict__ tw,
@@ -292,9 +293,9 @@ __global__ void __launch_bounds__(kCtThreads, 1)
     auto issue = [&](long t) {  // thread 0: both parities' runs of tile t
         const long bz = t / ((long)nz * ybs), rest = t - bz * nz * ybs;  // rest = n * ybs + yb
         const size_t off = (size_t)rest * kCtKx * kCtRows;
-        mbar_arrive_expect_tx(inb, (uint32_t)(2 * kCtHalf));
+        mbar_arrive_expect_tx(inb, (uint32_t)((TWO ? 2 : 1) * kCtHalf));
         bulk_g2s(smem_raw, in0 + bz * in_bstride + off, (uint32_t)kCtHalf, inb);
-        bulk_g2s(smem_raw + kCtHalf, in1 + bz * in_bstride + off, (uint32_t)kCtHalf, inb);
+        if (TWO) bulk_g2s(smem_raw + kCtHalf, in1 + bz * in_bstride + off, (uint32_t)kCtHalf, inb);
     };
 
     if (tid == 0) {
@@ -319,7 +320,8 @@ __global__ void __launch_bounds__(kCtThreads, 1)
         auto zk = [&](int kx) {
             const int pos = 2 * ((sq + (kx >> 1)) & 3);  // row pair sq's 16-byte position in the run
             const float4 v0 = *reinterpret_cast<const float4*>(t0 + kx * kCtRows + pos);
-            const float4 v1 = *reinterpret_cast<const float4*>(t1 + kx * kCtRows + pos);
+            const float4 v1 = TWO ? *reinterpret_cast<const float4*>(t1 + kx * kCtRows + pos)
+                                  : make_float4(0.f, 0.f, 0.f, 0.f);
             float2 A = make_float2(v0.x + v1.x, v0.y + v1.y), B = make_float2(v0.z + v1.z, v0.w + v1.w);
             if (!ha) A = make_float2(0.f, 0.f);
             if (!hb) B = make_float2(0.f, 0.f);
@@ -528,6 +530,19 @@ cudaError_t launch_row_c2r(int log_p, const void* in0, const void* in1, int I, i
     }
 }
 
+namespace {
+template <bool TWO>
+cudaError_t c2r_tiled_launch(int grid, const void* in0, const void* in1, int ny, int nz, float* out, size_t out_stride,
+                             int l_out, const void* tw, int log_t, cudaStream_t s, Batch b, int* err) {
+    constexpr auto k = row_c2r_tiled_kernel<TWO>;
+    cudaError_t e = ensure_smem_limit<k>();
+    if (e != cudaSuccess) return e;
+    k<<<grid, kCtThreads, kCtSmem, s>>>((const float2*)in0, (const float2*)in1, ny, nz, out, out_stride, l_out,
+                                        (const float2*)tw, log_t, b.in, b.out, b.count, err);
+    return cudaGetLastError();
+}
+}  // namespace
+
 cudaError_t launch_row_c2r_tiled(const void* in0, const void* in1, int ny, int nz, int kx_count, float* out,
                                  size_t out_stride, int l_out, const void* tw, int log_t, cudaStream_t s, Batch b,
                                  int* err) {
@@ -536,15 +551,11 @@ cudaError_t launch_row_c2r_tiled(const void* in0, const void* in1, int ny, int n
         return cudaErrorInvalidValue;
     const int sms = sm_count();
     if (sms <= 0) return cudaErrorInvalidValue;
-    constexpr auto k = row_c2r_tiled_kernel;
-    cudaError_t e = ensure_smem_limit<k>();
-    if (e != cudaSuccess) return e;
     const long ntiles = (long)b.count * nz * ny_blocks(ny);
     const int grid = (int)std::min<long>(ntiles, sms);
     if (grid == 0) return cudaSuccess;
-    k<<<grid, kCtThreads, kCtSmem, s>>>((const float2*)in0, (const float2*)in1, ny, nz, out, out_stride, l_out,
-                                        (const float2*)tw, log_t, b.in, b.out, b.count, err);
-    return cudaGetLastError();
+    return in1 ? c2r_tiled_launch<true>(grid, in0, in1, ny, nz, out, out_stride, l_out, tw, log_t, s, b, err)
+               : c2r_tiled_launch<false>(grid, in0, in1, ny, nz, out, out_stride, l_out, tw, log_t, s, b, err);
 }
 
 template cudaError_t launch_row_r2c<float>(int, const float*, size_t, size_t, int, int, int, void*, int, const void*,

@@ -197,8 +197,9 @@ cudaError_t launch_adjoint_wf512(const ColumnArgs& a, const void* Xr, const floa
 
 // Adjoint inverse rows from the tiled column output (ColumnArgs::z_tiled):
 // in_r[n][y / 8][kx][8] (swizzled as described there) for r = 0, 1 (in1 = in0 + one half), summed, kx
-// in [0, 1024]; out row (n, y) at out + (n * ny + y) * out_stride, first
-// l_out <= 1024 values.  FP32, P = 2048.  err as for the column kernels.
+// in [0, 1024]; in1 = nullptr: the single input in0.  Out row (n, y) at
+// out + (n * ny + y) * out_stride, first l_out <= 1024 values.  FP32,
+// P = 2048.  err as for the column kernels.
 cudaError_t launch_row_c2r_tiled(const void* in0, const void* in1, int ny, int nz, int kx_count, float* out,
                                  size_t out_stride, int l_out, const void* tw, int log_t, cudaStream_t s,
                                  Batch b, int* err);

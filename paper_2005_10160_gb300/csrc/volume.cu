@@ -39,8 +39,10 @@
 #include <new>
 #include <type_traits>
 
+#include "async_copy.cuh"
 #include "fft_block.cuh"
 #include "grav_internal.h"
+#include "warp_fft.cuh"
 
 namespace grav {
 
@@ -110,6 +112,39 @@ __global__ void __launch_bounds__(kVolThreads) vol_rows_kernel(const C* __restri
     }
 }
 
+// Pass D when pass E runs the tiled inverse row kernel (FP32, Px = 2048):
+// inverse column FFTs of the rows W[kx][r][ky] (r = c nz + t: R rows per kx),
+// the ny stations kept and written as V[r][y / 8][kx][8], row pair j of each
+// block of 8 rows at 16-byte position (j + kx / 2) % 4 of its kx run (rows
+// beyond ny zero): the layout launch_row_c2r_tiled reads with one bulk copy
+// per block.  A CTA transforms four kx of one r and writes 256 contiguous
+// bytes per block.
+constexpr int kYtSeqs = 4;
+template <int LOGN>
+__global__ void __launch_bounds__(kVolThreads) vol_yinv_tiled_kernel(const float2* __restrict__ in, int R, int kx_count,
+                                                                     int ny, float2* __restrict__ out,
+                                                                     const float2* __restrict__ tw, int tw_shift) {
+    constexpr int N = 1 << LOGN, SSTR = seq_stride<float2>(N);
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    float2* buf = reinterpret_cast<float2*>(smem_raw);
+    const int tid = threadIdx.x;
+    const int kx0 = blockIdx.x * kYtSeqs, r = blockIdx.y;
+    block_fft_from<float2, LOGN, kYtSeqs, kVolThreads, true>(buf, SSTR, tw, tw_shift, tid, [&](int sq, int m) {
+        const int kx = kx0 + sq;
+        return kx < kx_count ? in[((size_t)kx * R + r) * N + m] : make_float2(0.f, 0.f);
+    });
+    const int ybs = (ny + 7) >> 3;
+    for (int e = tid; e < ybs * kYtSeqs * 8; e += kVolThreads) {
+        const int slot = e & 7, sq = (e >> 3) & (kYtSeqs - 1), yb = e / (8 * kYtSeqs);
+        const int kx = kx0 + sq;
+        if (kx >= kx_count) continue;
+        const int j = ((slot >> 1) - (kx >> 1)) & 3;  // the row pair at this 16-byte position
+        const int y = 8 * yb + 2 * j + (slot & 1);
+        out[(((size_t)r * ybs + yb) * kx_count + kx) * 8 + slot] =
+            y < ny ? buf[sq * SSTR + sidx<float2>(y)] : make_float2(0.f, 0.f);
+    }
+}
+
 struct ZArgs {
     int nz, py, kx_count, ncomp;
     int jyc, jzc;          // stored spectra extents per kx: Py/2 + 1, Pz/2 + 1
@@ -151,7 +186,7 @@ __global__ void __launch_bounds__(z_threads(TI, LOGZ, sizeof(R) == 8), 2)
     C* tab = G + TI * SSTR;  // per-pass twiddles (fft_block.cuh)
     const int tid = threadIdx.x;
     const int grp = WARP ? tid >> 5 : 0, gtid = WARP ? (tid & 31) : tid;
-    const int kx = blockIdx.x, ky0 = blockIdx.y * TI;
+    const int kx = blockIdx.y, ky0 = blockIdx.x * TI;  // the ky tiles of one kx run together
     const int nz = a.nz, py = a.py;
     C* Fw = F + grp * GC * SSTR;  // this group's columns
     C* Gw = G + grp * GC * SSTR;
@@ -252,6 +287,211 @@ __global__ void __launch_bounds__(z_threads(TI, LOGZ, sizeof(R) == 8), 2)
     }
 }
 
+// Pass C for Pz = 256 in FP32, transforms in registers.  A warp owns two
+// columns of the tile; lane L works on column L / 16 with q = L % 16 and
+// holds 16 of its values.  256 = 16 x 16 (the four-step form):
+//   forward  x[q + 16 n2] -> 16-point DFT over n2 -> twiddle W_256^(q k2)
+//            -> transpose through the warp's shared area (q <-> k2)
+//            -> 16-point DFT over n1: lane q = k2 holds X[k2 + 16 k1] with
+//            k1 = bitrev4(j) in register j;
+//   inverse  from that layout: 16-point DFT over k1 -> twiddle W_256^(-a k2)
+//            -> transpose -> 16-point DFT over k2: lane q = a holds
+//            x[a + 16 b], b = bitrev4(j).
+// Pz = 256 >= 2 nz - 1 gives nz <= 128, so the inputs x[q + 16 n2] with
+// n2 >= 8 are zero (the first stage of the forward DFT only twiddles) and
+// the stations kept are x[a + 16 b] with b < 8 (the even registers: the last
+// stage of the inverse DFT keeps its sums).  Tiles of nz rows x 16 columns
+// move between HBM and shared memory in rows of 128 bytes; the CTA grid runs
+// the ky tiles of one kx next to each other, so each kx's spectra are read
+// from HBM once and served from L2 to both halves of every mirror pair.
+constexpr int kZ2Ti = 16, kZ2Warps = 8, kZ2Threads = 32 * kZ2Warps;
+constexpr int kZ2Str = kZ2Ti + 1;              // staging tile row stride (complex)
+constexpr int kZ2TrStr = 17;                   // transpose area row stride
+constexpr int kZ2TrWarp = 2 * 16 * kZ2TrStr;   // complex values of a warp's transpose area
+constexpr int kZ2MaxNz = 128;
+constexpr int kZ2Stage = kZ2MaxNz * kZ2Str;    // complex values of one staging tile
+constexpr size_t kZ2Smem = (size_t)(256 + kZ2Warps * kZ2TrWarp + 2 * kZ2Stage) * sizeof(float2);
+
+// 16-point DFT in registers, radix-2 decimation in frequency: natural order
+// in, u[j] = X[bitrev4(j)] out.  HALF: u[8..15] are zero on entry.  LOW:
+// only X[m] with m < 8 (the even registers) are wanted on exit.
+template <bool INV, bool HALF, bool LOW> __device__ __forceinline__ void dft16r(float2 (&u)[16]) {
+#pragma unroll
+    for (int h = 8; h >= 1; h >>= 1) {
+#pragma unroll
+        for (int b = 0; b < 16; b += 2 * h) {
+#pragma unroll
+            for (int i = 0; i < h; ++i) {
+                const float2 x0 = u[b + i];
+                if (HALF && h == 8) {
+                    u[b + i + h] = tw32<INV>(x0, 2 * i);
+                } else if (LOW && h == 1) {
+                    u[b + i] = cadd(x0, u[b + i + h]);
+                } else {
+                    const float2 x1 = u[b + i + h];
+                    u[b + i] = cadd(x0, x1);
+                    u[b + i + h] = tw32<INV>(csub(x0, x1), 2 * i * (8 / h));
+                }
+            }
+        }
+    }
+}
+
+template <bool ADJ>
+__global__ void __launch_bounds__(kZ2Threads, 2)
+    vol_z256_kernel(ZArgs a, const float2* __restrict__ in, float2* __restrict__ out, const float* __restrict__ spec3,
+                    const float2* __restrict__ tw) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    float2* tab = reinterpret_cast<float2*>(smem_raw);  // tab[r * 16 + c] = W_256^(r c)
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int col = lane >> 4, q = lane & 15;
+    float2* tr = tab + 256 + warp * kZ2TrWarp + col * 16 * kZ2TrStr;  // this column's transpose area
+    float2* stage = tab + 256 + kZ2Warps * kZ2TrWarp;                 // two [t][kZ2Str] tiles
+    const int ky0 = blockIdx.x * kZ2Ti, kx = blockIdx.y;
+    const int nz = a.nz, py = a.py;
+    const int ci = 2 * warp + col, ky = ky0 + ci;
+    const bool kyok = ky < py, fy = ky > py / 2;
+    const int jy = !kyok ? 0 : (fy ? py - ky : ky);
+
+    for (int e = tid; e < 256; e += kZ2Threads) tab[e] = tw[((e >> 4) * (e & 15)) << a.tw_shift];
+
+    // nz rows of the tile's 16 columns (zero beyond py) into a staging tile
+    auto load_tile = [&](float2* st, const float2* src) {
+        for (int e = tid; e < kZ2Ti * nz; e += kZ2Threads) {
+            const int n = e >> 4, i = e & 15;
+            st[n * kZ2Str + i] = (ky0 + i < py) ? src[(size_t)n * py + ky0 + i] : make_float2(0.f, 0.f);
+        }
+    };
+    // the same by per-thread asynchronous copies (one group per call)
+    auto issue_tile = [&](float2* st, const float2* src) {
+        for (int e = tid; e < kZ2Ti * nz; e += kZ2Threads) {
+            const int n = e >> 4, i = e & 15;
+            const bool ok = ky0 + i < py;
+            async8_g2s(st + n * kZ2Str + i, ok ? src + (size_t)n * py + ky0 + i : src, ok);
+        }
+        async8_commit();
+    };
+    auto store_tile = [&](const float2* st, float2* dst) {
+        for (int e = tid; e < kZ2Ti * nz; e += kZ2Threads) {
+            const int t = e >> 4, i = e & 15;
+            if (ky0 + i < py) dst[(size_t)t * py + ky0 + i] = st[t * kZ2Str + i];
+        }
+    };
+    // forward transform of this lane's column from a staging tile
+    auto fwd_fft = [&](const float2* st, float2 (&u)[16]) {
+#pragma unroll
+        for (int n2 = 0; n2 < 8; ++n2) {
+            const int n = q + 16 * n2;
+            u[n2] = n < nz ? st[n * kZ2Str + ci] : make_float2(0.f, 0.f);
+        }
+        dft16r<false, true, false>(u);
+#pragma unroll
+        for (int j = 0; j < 16; ++j) {
+            const int k2 = bitrev4(j);
+            tr[k2 * kZ2TrStr + q] = cmul(u[j], tab[k2 * 16 + q]);
+        }
+        __syncwarp();
+#pragma unroll
+        for (int n1 = 0; n1 < 16; ++n1) u[n1] = tr[q * kZ2TrStr + n1];
+        __syncwarp();
+        dft16r<false, false, false>(u);
+    };
+    // inverse transform in place; the stations t = q + 16 bitrev4(j) < 128
+    // are in the even registers j on exit
+    auto inv_fft = [&](float2 (&g)[16]) {
+        float2 h[16];
+#pragma unroll
+        for (int k1 = 0; k1 < 16; ++k1) h[k1] = g[bitrev4(k1)];
+        dft16r<true, false, false>(h);
+#pragma unroll
+        for (int j = 0; j < 16; ++j) {
+            const int aa = bitrev4(j);
+            tr[aa * kZ2TrStr + q] = cmul(h[j], cconj(tab[aa * 16 + q]));
+        }
+        __syncwarp();
+#pragma unroll
+        for (int k2 = 0; k2 < 16; ++k2) g[k2] = tr[q * kZ2TrStr + k2];
+        __syncwarp();
+        dft16r<true, false, true>(g);
+    };
+    auto put_stations = [&](float2* st, const float2 (&g)[16]) {
+#pragma unroll
+        for (int j = 0; j < 16; j += 2) {
+            const int t = q + 16 * bitrev4(j);
+            if (t < nz) st[t * kZ2Str + ci] = g[j];
+        }
+    };
+    // spectrum of slot c at (ky, kz = q + 16 bitrev4(j)) as the real v with
+    // S = v or S = i v
+    auto load_spec = [&](int c, float (&v)[16]) {
+        const float* base = spec3 + (((size_t)c * a.kx_count + kx) * a.jyc + jy) * a.jzc;
+        const bool ov = (a.oddv_mask >> c) & 1u, ow = (a.oddw_mask >> c) & 1u;
+#pragma unroll
+        for (int j = 0; j < 16; ++j) {
+            const int kz = q + 16 * bitrev4(j);
+            const bool fz = kz > 128;
+            const float val = kyok ? __ldg(base + (fz ? 256 - kz : kz)) : 0.f;
+            v[j] = ((fy && ov) != (fz && ow)) ? -val : val;
+        }
+    };
+
+    if constexpr (!ADJ) {
+        float2* st_in = stage + kZ2Stage;
+        load_tile(st_in, in + (size_t)kx * nz * py);
+        __syncthreads();  // the tile and the twiddle table are in place
+        float2 X[16];
+        fwd_fft(st_in, X);
+        float v[16];
+        load_spec(0, v);
+        for (int c = 0; c < a.ncomp; ++c) {
+            const bool imag = (a.imag3_mask >> c) & 1u;
+            float2 g[16];
+#pragma unroll
+            for (int j = 0; j < 16; ++j)
+                g[j] = imag ? make_float2(-v[j] * X[j].y, v[j] * X[j].x) : make_float2(v[j] * X[j].x, v[j] * X[j].y);
+            if (c + 1 < a.ncomp) load_spec(c + 1, v);  // in flight during the transform
+            inv_fft(g);
+            // staging tile c % 2: its last reader (the store of component
+            // c - 2, or the input read for c = 1) finished before the
+            // previous barrier
+            float2* st = stage + (c & 1) * kZ2Stage;
+            put_stations(st, g);
+            __syncthreads();
+            store_tile(st, out + ((size_t)kx * a.ncomp + c) * nz * py);
+        }
+    } else {
+        float2 acc[16];
+#pragma unroll
+        for (int j = 0; j < 16; ++j) acc[j] = make_float2(0.f, 0.f);
+        // component c's tile is copied into staging tile c % 2 while
+        // component c - 1 is transformed
+        issue_tile(stage, in + (size_t)kx * a.ncomp * nz * py);
+        for (int c = 0; c < a.ncomp; ++c) {
+            float2* st = stage + (c & 1) * kZ2Stage;
+            float v[16];
+            load_spec(c, v);
+            async8_wait_all();
+            // tile c has landed everywhere, and every read of tile c - 1
+            // (staging tile (c + 1) % 2) is done
+            __syncthreads();
+            if (c + 1 < a.ncomp)
+                issue_tile(stage + ((c + 1) & 1) * kZ2Stage, in + ((size_t)kx * a.ncomp + c + 1) * nz * py);
+            float2 f[16];
+            fwd_fft(st, f);
+            const bool imag = (a.imag3_mask >> c) & 1u;
+#pragma unroll
+            for (int j = 0; j < 16; ++j)  // conj(S) f: S = v or S = i v
+                acc[j] = imag ? make_float2(acc[j].x + v[j] * f[j].y, acc[j].y - v[j] * f[j].x)
+                              : make_float2(acc[j].x + v[j] * f[j].x, acc[j].y + v[j] * f[j].y);
+        }
+        inv_fft(acc);
+        float2* st = stage + (a.ncomp & 1) * kZ2Stage;  // not the tile the last component read
+        put_stations(st, acc);
+        __syncthreads();
+        store_tile(st, out + (size_t)kx * nz * py);
+    }
+}
+
 // Plan creation, column step: y-FFT of the kernel row transforms
 // Ehat[kx][o][b] (o < cnt layers of one component, b < py) and the real
 // (imag2 = false) or imaginary part of ky <= Py/2, stored as
@@ -334,6 +574,30 @@ cudaError_t rows_launch(const void* in, size_t in_stride, int l_in, void* out, s
 
 #define GRAV_VOL_LOG_CASES(X) X(2) X(3) X(4) X(5) X(6) X(7) X(8) X(9) X(10) X(11)
 
+template <int LOGN>
+cudaError_t yinv_tiled_launch(const void* in, int R, int kx_count, int ny, void* out, const void* tw, int tw_shift,
+                              cudaStream_t s) {
+    constexpr auto k = vol_yinv_tiled_kernel<LOGN>;
+    const size_t smem = (size_t)kYtSeqs * seq_stride<float2>(1 << LOGN) * sizeof(float2);
+    cudaError_t e = ensure_smem_limit<k>();
+    if (e != cudaSuccess) return e;
+    const dim3 grid((kx_count + kYtSeqs - 1) / kYtSeqs, R);
+    if (grid.x == 0 || grid.y == 0) return cudaSuccess;
+    k<<<grid, kVolThreads, smem, s>>>((const float2*)in, R, kx_count, ny, (float2*)out, (const float2*)tw, tw_shift);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_vol_yinv_tiled(int logn, const void* in, int R, int kx_count, int ny, void* out, const void* tw,
+                                  int log_t, cudaStream_t s) {
+    switch (logn) {
+#define CASE(L) \
+    case L: return yinv_tiled_launch<L>(in, R, kx_count, ny, out, tw, log_t - L, s);
+        GRAV_VOL_LOG_CASES(CASE)
+#undef CASE
+        default: return cudaErrorInvalidValue;
+    }
+}
+
 template <typename C, bool INV>
 cudaError_t launch_vol_rows(int logn, const void* in, size_t in_stride, int l_in, void* out, size_t out_stride,
                             int l_out, long rows, const void* tw, int log_t, cudaStream_t s) {
@@ -349,14 +613,23 @@ cudaError_t launch_vol_rows(int logn, const void* in, size_t in_stride, int l_in
 template <typename R, int LOGZ, bool ADJ>
 cudaError_t z_launch(const ZArgs& a, const void* in, void* out, const R* spec3, const void* tw, cudaStream_t s) {
     using C = typename cplx<R>::type;
-    constexpr int TI = z_tile<C>(LOGZ);
-    constexpr int NT = z_threads(TI, LOGZ, sizeof(R) == 8);
-    constexpr auto k = vol_z_kernel<R, LOGZ, TI, ADJ>;
-    const size_t smem = ((size_t)2 * TI * seq_stride<C>(1 << LOGZ) + tw_tab_len(LOGZ)) * sizeof(C);
-    cudaError_t e = ensure_smem_limit<k>();
-    if (e != cudaSuccess) return e;
-    k<<<dim3(a.kx_count, (a.py + TI - 1) / TI), NT, smem, s>>>(a, (const C*)in, (C*)out, spec3, (const C*)tw);
-    return cudaGetLastError();
+    if constexpr (std::is_same<R, float>::value && LOGZ == 8) {
+        constexpr auto k = vol_z256_kernel<ADJ>;
+        cudaError_t e = ensure_smem_limit<k>();
+        if (e != cudaSuccess) return e;
+        k<<<dim3((a.py + kZ2Ti - 1) / kZ2Ti, a.kx_count), kZ2Threads, kZ2Smem, s>>>(a, (const float2*)in, (float2*)out,
+                                                                                   spec3, (const float2*)tw);
+        return cudaGetLastError();
+    } else {
+        constexpr int TI = z_tile<C>(LOGZ);
+        constexpr int NT = z_threads(TI, LOGZ, sizeof(R) == 8);
+        constexpr auto k = vol_z_kernel<R, LOGZ, TI, ADJ>;
+        const size_t smem = ((size_t)2 * TI * seq_stride<C>(1 << LOGZ) + tw_tab_len(LOGZ)) * sizeof(C);
+        cudaError_t e = ensure_smem_limit<k>();
+        if (e != cudaSuccess) return e;
+        k<<<dim3((a.py + TI - 1) / TI, a.kx_count), NT, smem, s>>>(a, (const C*)in, (C*)out, spec3, (const C*)tw);
+        return cudaGetLastError();
+    }
 }
 
 template <typename R, bool ADJ>
@@ -432,8 +705,14 @@ size_t vol_ws_a_elems(const grav_plan* p) {
 }
 size_t vol_ws_b_elems(const grav_plan* p) {
     const size_t kx = p->kx_count, nz = p->nz, nc = p->ncomp;
-    return kx * nc * nz * p->py;  // U' (the largest of U, U', V and V')
+    const size_t u = kx * nc * nz * p->py;                          // U' (the largest of U, U', V and V')
+    const size_t v = kx * nc * nz * (((size_t)p->ny + 7) / 8 * 8);  // V in the tiled layout
+    return u > v ? u : v;
 }
+
+// Whether passes D and E take the tiled layout and the tiled inverse row
+// kernel (FP32 plans with Px = 2048).
+bool vol_tiled_rows(const grav_plan* p) { return !p->fp64 && p->kx_count == 1025 && p->nx <= 1024; }
 
 template <typename R>
 int make_spectra3(grav_plan* p) {
@@ -549,6 +828,17 @@ int run_forward3d(grav_plan* p, const void* rho, void* out, cudaStream_t s) {
     // C: z, product, inverse z
     e = launch_vol_z<R, false>(p->log_pz, z_args(p), B, A, (const R*)p->spec, p->tw, s);
     if (e != cudaSuccess) return cuda_fail(e, "equal-dimension forward: layer transforms");
+    if constexpr (std::is_same<R, float>::value) {
+        if (vol_tiled_rows(p)) {
+            // D: inverse y into the tiled layout; E: inverse x from it
+            e = launch_vol_yinv_tiled(p->log_py, A, (int)(nc * nz), p->kx_count, p->ny, B, p->tw, p->log_t, s);
+            if (e != cudaSuccess) return cuda_fail(e, "equal-dimension forward: inverse column transforms");
+            e = launch_row_c2r_tiled(B, nullptr, p->ny, (int)(nc * nz), p->kx_count, (float*)out, (size_t)p->nx,
+                                     p->nx, p->tw, p->log_t, s, Batch(), p->err_flag);
+            if (e != cudaSuccess) return cuda_fail(e, "equal-dimension forward: inverse row transforms");
+            return GRAV_OK;
+        }
+    }
     // D: inverse y
     e = launch_vol_rows<C, true>(p->log_py, A, p->py, p->py, B, p->ny_pad, p->ny, (long)(kx * nc * nz), p->tw,
                                  p->log_t, s);
@@ -575,6 +865,16 @@ int run_adjoint3d(grav_plan* p, const void* r, void* grad, cudaStream_t s) {
     if (e != cudaSuccess) return cuda_fail(e, "equal-dimension adjoint: column transforms");
     e = launch_vol_z<R, true>(p->log_pz, z_args(p), B, A, (const R*)p->spec, p->tw, s);
     if (e != cudaSuccess) return cuda_fail(e, "equal-dimension adjoint: layer transforms");
+    if constexpr (std::is_same<R, float>::value) {
+        if (vol_tiled_rows(p)) {
+            e = launch_vol_yinv_tiled(p->log_py, A, (int)nz, p->kx_count, p->ny, B, p->tw, p->log_t, s);
+            if (e != cudaSuccess) return cuda_fail(e, "equal-dimension adjoint: inverse column transforms");
+            e = launch_row_c2r_tiled(B, nullptr, p->ny, p->nz, p->kx_count, (float*)grad, (size_t)p->nx, p->nx,
+                                     p->tw, p->log_t, s, Batch(), p->err_flag);
+            if (e != cudaSuccess) return cuda_fail(e, "equal-dimension adjoint: inverse row transforms");
+            return GRAV_OK;
+        }
+    }
     e = launch_vol_rows<C, true>(p->log_py, A, p->py, p->py, B, p->ny_pad, p->ny, (long)(kx * nz), p->tw, p->log_t, s);
     if (e != cudaSuccess) return cuda_fail(e, "equal-dimension adjoint: inverse column transforms");
     e = launch_row_c2r<R>(p->log_px, B, nullptr, p->ny, p->nz, p->ny_pad, (R*)grad, (size_t)p->nx, p->nx, p->tw,

@@ -49,8 +49,13 @@ def _adjoint(mesh, comps, r, fp64):
         return g.cpu().double().numpy()
 
 
+# (5, 4, 70) .. (3, 11, 65) reach the 256-point layer transform (65 <= nz <=
+# 128) held in registers, with fewer y columns than one tile of it (ny = 1, 4)
+# and a ragged one; (513, 3, 2) the tiled inverse y and x passes of FP32 plans
+# with Px = 2048, ny short of one block of 8 rows
 SMALL = [(1, 1, 1, 10.0, 10.0, 10.0, 1.0), (5, 4, 3, 20.0, 25.0, 10.0, 1.0), (9, 1, 4, 10.0, 10.0, 15.0, 1.0),
-         (3, 11, 2, 12.0, 10.0, 30.0, 1.0), (17, 13, 9, 10.0, 12.0, 8.0, 1.0)]
+         (3, 11, 2, 12.0, 10.0, 30.0, 1.0), (17, 13, 9, 10.0, 12.0, 8.0, 1.0), (5, 4, 70, 20.0, 25.0, 10.0, 1.0),
+         (9, 1, 100, 10.0, 10.0, 15.0, 1.0), (3, 11, 65, 12.0, 10.0, 30.0, 1.0), (513, 3, 2, 10.0, 10.0, 10.0, 1.0)]
 
 
 @pytest.mark.parametrize("mesh", SMALL)
@@ -95,9 +100,12 @@ def test_component_subsets(gravlib, orc, comps):
 
 
 # every transform length of the implementation: 2048-point x rows (the FP32
-# warp-transform row kernel), 2048-point y columns, 1024-point z columns
+# warp-transform row kernel), 2048-point y columns, 1024-point z columns, and
+# the register-resident 256-point z columns over many tiles (nz = 128, the
+# most that length holds, and nz = 100)
 LARGE = [(520, 9, 5, 20.0, 20.0, 10.0, 1.0), (12, 600, 6, 20.0, 15.0, 10.0, 1.0), (6, 5, 300, 20.0, 20.0, 5.0, 1.0),
-         (64, 48, 40, 20.0, 20.0, 20.0, 1.0)]
+         (64, 48, 40, 20.0, 20.0, 20.0, 1.0), (40, 36, 128, 20.0, 20.0, 10.0, 1.0), (33, 70, 100, 25.0, 20.0, 10.0, 1.0),
+         (600, 13, 70, 20.0, 20.0, 10.0, 1.0)]
 
 
 @pytest.mark.parametrize("mesh", LARGE)
@@ -126,9 +134,10 @@ def test_large_sizes_at_sampled_stations(gravlib, orc, mesh, fp64, tol):
     assert np.linalg.norm(g[cells] - gref) <= tol * np.linalg.norm(gref)
 
 
+@pytest.mark.parametrize("mesh", [(33, 20, 17, 10.0, 10.0, 10.0, 1.0), (20, 18, 90, 10.0, 10.0, 10.0, 1.0),
+                                  (530, 10, 6, 10.0, 10.0, 10.0, 1.0)])
 @pytest.mark.parametrize("fp64,tol", [(True, 1e-12), (False, 1e-5)])
-def test_dot_product_identity(gravlib, fp64, tol):
-    mesh = (33, 20, 17, 10.0, 10.0, 10.0, 1.0)
+def test_dot_product_identity(gravlib, mesh, fp64, tol):
     nx, ny, nz = mesh[:3]
     dt = torch.float64 if fp64 else torch.float32
     gen = torch.Generator().manual_seed(3)
