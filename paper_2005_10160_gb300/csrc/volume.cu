@@ -36,6 +36,7 @@
 //   E  x: inverse row transforms (C2R, row_c2r)           -> out[c][t][y][x]
 // The adjoint runs the same passes from r[c][t][y][x], multiplies by the
 // conjugate spectra and sums over components in pass C (the transpose).
+#include <algorithm>
 #include <new>
 #include <type_traits>
 
@@ -142,6 +143,123 @@ __global__ void __launch_bounds__(kVolThreads) vol_yinv_tiled_kernel(const float
         const int y = 8 * yb + 2 * j + (slot & 1);
         out[(((size_t)r * ybs + yb) * kx_count + kx) * 8 + slot] =
             y < ny ? buf[sq * SSTR + sidx<float2>(y)] : make_float2(0.f, 0.f);
+    }
+}
+
+// Passes B and D for Py = 2048 in FP32 (meshes with 513 <= ny <= 1024), a
+// pair of warps per row, each running one 1024-point transform in
+// registers (warp_fft1024).
+//   forward (ny <= 1024 nonzero inputs -> 2048 outputs): warp p computes
+//     Z(2k + p) = sum_{y < 1024} (z[y] W_2048^(p y)) W_1024^(y k);
+//   inverse (2048 inputs -> the first 1024 outputs): warp p transforms the
+//     samples Z(2k + p), and z[m] = E(m) + W_2048^(-m) O(m) for the even (E)
+//     and odd (O) sample transforms.
+// The two halves meet in shared memory: the forward writes each row as
+// (Z(2k), Z(2k + 1)) pairs of 16 bytes, the inverse writes the tiled layout
+// of vol_yinv_tiled_kernel (four kx of one r per group).  Persistent CTAs,
+// two per SM.
+constexpr int kYwRows = 4, kYwThreads = 64 * kYwRows;
+constexpr int kYwArea = kWarpFftSlot + 2;  // areas 4 banks apart
+constexpr size_t kYwSmem = (size_t)(2 * kYwRows * kYwArea + 2 * 1024) * sizeof(float2);
+
+// barrier of the two warps of row pair `id` (ids 1 .. 4; 0 is __syncthreads)
+__device__ __forceinline__ void pair_sync(int id) { asm volatile("bar.sync %0, 64;" ::"r"(id) : "memory"); }
+
+// t2[k1 32 + n] = W_1024^(k1 n) (warp_fft1024), t1[y] = W_2048^y (y < 1024)
+__device__ __forceinline__ void yw_tables(float2* t2, float2* t1, const float2* __restrict__ tw, int log_t, int tid) {
+    for (int e = tid; e < 1024; e += kYwThreads) {
+        t2[e] = tw[(((e >> 5) * (e & 31)) & 1023) << (log_t - 10)];
+        t1[e] = tw[e << (log_t - 11)];
+    }
+}
+
+__global__ void __launch_bounds__(kYwThreads, 2)
+    vol_yfwd2048_kernel(const float2* __restrict__ in, size_t in_stride, int l_in, float2* __restrict__ out,
+                        size_t out_stride, long rows, const float2* __restrict__ tw, int log_t) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    float2* areas = reinterpret_cast<float2*>(smem_raw);
+    float2* t2 = areas + 2 * kYwRows * kYwArea;
+    float2* t1 = t2 + 1024;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int sq = warp >> 1, p = warp & 1;
+    yw_tables(t2, t1, tw, log_t, tid);
+    __syncthreads();
+    float2* tr = areas + warp * kYwArea;
+    const float2* za = areas + 2 * sq * kYwArea;  // Z(2k) of this row
+    const float2* zb = za + kYwArea;              // Z(2k + 1)
+    for (long g = blockIdx.x; g * kYwRows < rows; g += gridDim.x) {
+        const long row = g * kYwRows + sq;
+        const bool ok = row < rows;
+        const float2* src = in + (size_t)(ok ? row : 0) * in_stride;
+        float2 u[32];
+#pragma unroll
+        for (int n1 = 0; n1 < 32; ++n1) {
+            const int y = 32 * n1 + lane;
+            u[n1] = (ok && y < l_in) ? src[y] : make_float2(0.f, 0.f);
+        }
+        if (p) {
+#pragma unroll
+            for (int n1 = 0; n1 < 32; ++n1) u[n1] = cmul(u[n1], t1[32 * n1 + lane]);
+        }
+        warp_fft1024<false>(u, tr, t2, lane);  // u[j] = Z(2 (lane + 32 bitrev5(j)) + p)
+#pragma unroll
+        for (int j = 0; j < 32; ++j) tr[lane + 32 * bitrev5(j)] = u[j];
+        pair_sync(1 + sq);
+        if (ok) {
+            float4* dst = reinterpret_cast<float4*>(out + (size_t)row * out_stride);
+#pragma unroll 4
+            for (int i = 0; i < 16; ++i) {
+                const int k = 512 * p + 32 * i + lane;
+                const float2 a = za[k], b = zb[k];
+                dst[k] = make_float4(a.x, a.y, b.x, b.y);
+            }
+        }
+        pair_sync(1 + sq);  // both halves are read before the areas are reused
+    }
+}
+
+__global__ void __launch_bounds__(kYwThreads, 2)
+    vol_yinv2048_tiled_kernel(const float2* __restrict__ in, int R, int kx_count, int ny, float2* __restrict__ out,
+                              const float2* __restrict__ tw, int log_t) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    float2* areas = reinterpret_cast<float2*>(smem_raw);
+    float2* t2 = areas + 2 * kYwRows * kYwArea;
+    float2* t1 = t2 + 1024;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int sq = warp >> 1, p = warp & 1;
+    yw_tables(t2, t1, tw, log_t, tid);
+    __syncthreads();
+    float2* tr = areas + warp * kYwArea;
+    const int kxg = (kx_count + kYwRows - 1) / kYwRows;
+    const int ybs = (ny + 7) >> 3;
+    const long groups = (long)kxg * R;
+    for (long g = blockIdx.x; g < groups; g += gridDim.x) {
+        const int r = (int)(g / kxg), kx0 = (int)(g - (long)r * kxg) * kYwRows;
+        const int kx = kx0 + sq;
+        const bool ok = kx < kx_count;
+        const float2* src = in + ((size_t)(ok ? kx : 0) * R + r) * 2048 + p;
+        float2 u[32];
+#pragma unroll
+        for (int n1 = 0; n1 < 32; ++n1) u[n1] = ok ? src[2 * (32 * n1 + lane)] : make_float2(0.f, 0.f);
+        warp_fft1024<true>(u, tr, t2, lane);  // u[j] = E or O at m = lane + 32 bitrev5(j)
+        if (p) {
+#pragma unroll
+            for (int j = 0; j < 32; ++j) u[j] = cmul(u[j], cconj(t1[lane + 32 * bitrev5(j)]));
+        }
+#pragma unroll
+        for (int j = 0; j < 32; ++j) tr[lane + 32 * bitrev5(j)] = u[j];
+        __syncthreads();  // E and W^-m O of all four rows are in place
+        for (int e = tid; e < ybs * kYwRows * 8; e += kYwThreads) {
+            const int slot = e & 7, s = (e >> 3) & (kYwRows - 1), yb = e / (8 * kYwRows);
+            const int kxs = kx0 + s;
+            if (kxs >= kx_count) continue;
+            const int jj = ((slot >> 1) - (kxs >> 1)) & 3;  // the row pair at this 16-byte position
+            const int y = 8 * yb + 2 * jj + (slot & 1);
+            float2 z = make_float2(0.f, 0.f);
+            if (y < ny) z = cadd(areas[2 * s * kYwArea + y], areas[(2 * s + 1) * kYwArea + y]);
+            out[(((size_t)r * ybs + yb) * kx_count + kxs) * 8 + slot] = z;
+        }
+        __syncthreads();  // the areas are rewritten by the next group
     }
 }
 
@@ -587,8 +705,25 @@ cudaError_t yinv_tiled_launch(const void* in, int R, int kx_count, int ny, void*
     return cudaGetLastError();
 }
 
+// persistent grid: two CTAs per SM, at most one per group of rows
+int yw_grid(long groups) {
+    int dev = 0, sms = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+        return 0;
+    return (int)std::min<long>(groups, 2L * sms);
+}
+
 cudaError_t launch_vol_yinv_tiled(int logn, const void* in, int R, int kx_count, int ny, void* out, const void* tw,
                                   int log_t, cudaStream_t s) {
+    if (logn == 11 && ny <= 1024) {
+        constexpr auto k = vol_yinv2048_tiled_kernel;
+        cudaError_t e = ensure_smem_limit<k>();
+        if (e != cudaSuccess) return e;
+        const int grid = yw_grid((long)((kx_count + kYwRows - 1) / kYwRows) * R);
+        if (grid <= 0) return R ? cudaErrorInvalidValue : cudaSuccess;
+        k<<<grid, kYwThreads, kYwSmem, s>>>((const float2*)in, R, kx_count, ny, (float2*)out, (const float2*)tw, log_t);
+        return cudaGetLastError();
+    }
     switch (logn) {
 #define CASE(L) \
     case L: return yinv_tiled_launch<L>(in, R, kx_count, ny, out, tw, log_t - L, s);
@@ -608,6 +743,26 @@ cudaError_t launch_vol_rows(int logn, const void* in, size_t in_stride, int l_in
 #undef CASE
         default: return cudaErrorInvalidValue;
     }
+}
+
+// Pass B (and the adjoint's): column FFTs of `rows` rows of l_in <= ny
+// values (row stride in_stride) into rows of Py values (stride out_stride).
+template <typename C>
+cudaError_t launch_vol_yfwd(int logn, const void* in, size_t in_stride, int l_in, void* out, size_t out_stride,
+                            long rows, const void* tw, int log_t, cudaStream_t s) {
+    if constexpr (std::is_same<C, float2>::value) {
+        if (logn == 11 && l_in <= 1024 && out_stride % 2 == 0 && (reinterpret_cast<uintptr_t>(out) & 15) == 0) {
+            constexpr auto k = vol_yfwd2048_kernel;
+            cudaError_t e = ensure_smem_limit<k>();
+            if (e != cudaSuccess) return e;
+            const int grid = yw_grid((rows + kYwRows - 1) / kYwRows);
+            if (grid <= 0) return rows ? cudaErrorInvalidValue : cudaSuccess;
+            k<<<grid, kYwThreads, kYwSmem, s>>>((const float2*)in, in_stride, l_in, (float2*)out, out_stride, rows,
+                                                (const float2*)tw, log_t);
+            return cudaGetLastError();
+        }
+    }
+    return launch_vol_rows<C, false>(logn, in, in_stride, l_in, out, out_stride, (int)out_stride, rows, tw, log_t, s);
 }
 
 template <typename R, int LOGZ, bool ADJ>
@@ -823,7 +978,7 @@ int run_forward3d(grav_plan* p, const void* rho, void* out, cudaStream_t s) {
                           p->ny_pad, p->tw, p->log_t, s, Batch(), p->err_flag);
     if (e != cudaSuccess) return cuda_fail(e, "equal-dimension forward: row transforms");
     // B: y
-    e = launch_vol_rows<C, false>(p->log_py, A, p->ny_pad, p->ny, B, p->py, p->py, (long)(kx * nz), p->tw, p->log_t, s);
+    e = launch_vol_yfwd<C>(p->log_py, A, p->ny_pad, p->ny, B, p->py, (long)(kx * nz), p->tw, p->log_t, s);
     if (e != cudaSuccess) return cuda_fail(e, "equal-dimension forward: column transforms");
     // C: z, product, inverse z
     e = launch_vol_z<R, false>(p->log_pz, z_args(p), B, A, (const R*)p->spec, p->tw, s);
@@ -860,8 +1015,7 @@ int run_adjoint3d(grav_plan* p, const void* r, void* grad, cudaStream_t s) {
     e = launch_row_r2c<R>(p->log_px, (const R*)r, (size_t)p->ny * p->nx, (size_t)p->nx, p->nx, p->ny, (int)(nc * nz),
                           A, p->ny_pad, p->tw, p->log_t, s, Batch(), p->err_flag);
     if (e != cudaSuccess) return cuda_fail(e, "equal-dimension adjoint: row transforms");
-    e = launch_vol_rows<C, false>(p->log_py, A, p->ny_pad, p->ny, B, p->py, p->py, (long)(kx * nc * nz), p->tw,
-                                  p->log_t, s);
+    e = launch_vol_yfwd<C>(p->log_py, A, p->ny_pad, p->ny, B, p->py, (long)(kx * nc * nz), p->tw, p->log_t, s);
     if (e != cudaSuccess) return cuda_fail(e, "equal-dimension adjoint: column transforms");
     e = launch_vol_z<R, true>(p->log_pz, z_args(p), B, A, (const R*)p->spec, p->tw, s);
     if (e != cudaSuccess) return cuda_fail(e, "equal-dimension adjoint: layer transforms");

@@ -102,10 +102,12 @@ def test_component_subsets(gravlib, orc, comps):
 # every transform length of the implementation: 2048-point x rows (the FP32
 # warp-transform row kernel), 2048-point y columns, 1024-point z columns, and
 # the register-resident 256-point z columns over many tiles (nz = 128, the
-# most that length holds, and nz = 100)
+# most that length holds, and nz = 100), the warp-pair 2048-point y transforms
+# (513 <= ny <= 1024) and, with 513 <= nx <= 1024 as well, the tiled inverse
+# y and x passes
 LARGE = [(520, 9, 5, 20.0, 20.0, 10.0, 1.0), (12, 600, 6, 20.0, 15.0, 10.0, 1.0), (6, 5, 300, 20.0, 20.0, 5.0, 1.0),
          (64, 48, 40, 20.0, 20.0, 20.0, 1.0), (40, 36, 128, 20.0, 20.0, 10.0, 1.0), (33, 70, 100, 25.0, 20.0, 10.0, 1.0),
-         (600, 13, 70, 20.0, 20.0, 10.0, 1.0)]
+         (600, 13, 70, 20.0, 20.0, 10.0, 1.0), (520, 530, 3, 20.0, 20.0, 10.0, 1.0)]
 
 
 @pytest.mark.parametrize("mesh", LARGE)
@@ -135,7 +137,7 @@ def test_large_sizes_at_sampled_stations(gravlib, orc, mesh, fp64, tol):
 
 
 @pytest.mark.parametrize("mesh", [(33, 20, 17, 10.0, 10.0, 10.0, 1.0), (20, 18, 90, 10.0, 10.0, 10.0, 1.0),
-                                  (530, 10, 6, 10.0, 10.0, 10.0, 1.0)])
+                                  (530, 10, 6, 10.0, 10.0, 10.0, 1.0), (514, 600, 3, 10.0, 10.0, 10.0, 1.0)])
 @pytest.mark.parametrize("fp64,tol", [(True, 1e-12), (False, 1e-5)])
 def test_dot_product_identity(gravlib, mesh, fp64, tol):
     nx, ny, nz = mesh[:3]
