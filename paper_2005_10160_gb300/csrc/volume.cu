@@ -418,11 +418,11 @@ __global__ void __launch_bounds__(z_threads(TI, LOGZ, sizeof(R) == 8), 2)
 // Pz = 256 >= 2 nz - 1 gives nz <= 128, so the inputs x[q + 16 n2] with
 // n2 >= 8 are zero (the first stage of the forward DFT only twiddles) and
 // the stations kept are x[a + 16 b] with b < 8 (the even registers: the last
-// stage of the inverse DFT keeps its sums).  Tiles of nz rows x 16 columns
-// move between HBM and shared memory in rows of 128 bytes; the CTA grid runs
+// stage of the inverse DFT keeps its sums).  Tiles of nz rows x 8 columns (a
+// CTA of four warps) move between HBM and shared memory in rows of 64 bytes; the CTA grid runs
 // the ky tiles of one kx next to each other, so each kx's spectra are read
 // from HBM once and served from L2 to both halves of every mirror pair.
-constexpr int kZ2Ti = 16, kZ2Warps = 8, kZ2Threads = 32 * kZ2Warps;
+constexpr int kZ2Warps = 4, kZ2Ti = 2 * kZ2Warps, kZ2Threads = 32 * kZ2Warps;
 constexpr int kZ2Str = kZ2Ti + 1;              // staging tile row stride (complex)
 constexpr int kZ2TrStr = 17;                   // transpose area row stride
 constexpr int kZ2TrWarp = 2 * 16 * kZ2TrStr;   // complex values of a warp's transpose area
@@ -456,7 +456,7 @@ template <bool INV, bool HALF, bool LOW> __device__ __forceinline__ void dft16r(
 }
 
 template <bool ADJ>
-__global__ void __launch_bounds__(kZ2Threads, 2)
+__global__ void __launch_bounds__(kZ2Threads, 16 / kZ2Warps)
     vol_z256_kernel(ZArgs a, const float2* __restrict__ in, float2* __restrict__ out, const float* __restrict__ spec3,
                     const float2* __restrict__ tw) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -476,14 +476,14 @@ __global__ void __launch_bounds__(kZ2Threads, 2)
     // nz rows of the tile's 16 columns (zero beyond py) into a staging tile
     auto load_tile = [&](float2* st, const float2* src) {
         for (int e = tid; e < kZ2Ti * nz; e += kZ2Threads) {
-            const int n = e >> 4, i = e & 15;
+            const int n = e / kZ2Ti, i = e % kZ2Ti;
             st[n * kZ2Str + i] = (ky0 + i < py) ? src[(size_t)n * py + ky0 + i] : make_float2(0.f, 0.f);
         }
     };
     // the same by per-thread asynchronous copies (one group per call)
     auto issue_tile = [&](float2* st, const float2* src) {
         for (int e = tid; e < kZ2Ti * nz; e += kZ2Threads) {
-            const int n = e >> 4, i = e & 15;
+            const int n = e / kZ2Ti, i = e % kZ2Ti;
             const bool ok = ky0 + i < py;
             async8_g2s(st + n * kZ2Str + i, ok ? src + (size_t)n * py + ky0 + i : src, ok);
         }
@@ -491,7 +491,7 @@ __global__ void __launch_bounds__(kZ2Threads, 2)
     };
     auto store_tile = [&](const float2* st, float2* dst) {
         for (int e = tid; e < kZ2Ti * nz; e += kZ2Threads) {
-            const int t = e >> 4, i = e & 15;
+            const int t = e / kZ2Ti, i = e % kZ2Ti;
             if (ky0 + i < py) dst[(size_t)t * py + ky0 + i] = st[t * kZ2Str + i];
         }
     };
