@@ -418,10 +418,11 @@ __global__ void __launch_bounds__(z_threads(TI, LOGZ, sizeof(R) == 8), 2)
 // Pz = 256 >= 2 nz - 1 gives nz <= 128, so the inputs x[q + 16 n2] with
 // n2 >= 8 are zero (the first stage of the forward DFT only twiddles) and
 // the stations kept are x[a + 16 b] with b < 8 (the even registers: the last
-// stage of the inverse DFT keeps its sums).  Tiles of nz rows x 8 columns (a
-// CTA of four warps) move between HBM and shared memory in rows of 64 bytes; the CTA grid runs
-// the ky tiles of one kx next to each other, so each kx's spectra are read
-// from HBM once and served from L2 to both halves of every mirror pair.
+// stage of the inverse DFT keeps its sums).  Tiles of nz rows x 8 columns
+// (a CTA of four warps) move between HBM and shared memory in rows of 64
+// bytes; the CTA grid runs the ky tiles of one kx next to each other, so each
+// kx's spectra are read from HBM once and served from L2 to both halves of
+// every mirror pair.
 constexpr int kZ2Warps = 4, kZ2Ti = 2 * kZ2Warps, kZ2Threads = 32 * kZ2Warps;
 constexpr int kZ2Str = kZ2Ti + 1;              // staging tile row stride (complex)
 constexpr int kZ2TrStr = 17;                   // transpose area row stride
