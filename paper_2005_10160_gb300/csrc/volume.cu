@@ -21,10 +21,11 @@
 // the height h' = -(nz - 1/2) dz: its z-levels (nz - 1/2 - j) dz and
 // (nz - 3/2 - j) dz are the station-minus-corner depths (1/2 - w) dz and
 // (-1/2 - w) dz.  Per component and chunk of layers: generate and embed
-// (kernel_gen), transform the rows (x, row_r2c), transform the columns (y)
-// and keep the real or imaginary part of ky <= Py/2 per layer; then
-// transform each (kx, ky) sequence over the layers along z and keep the real
-// or imaginary part of kz <= Pz/2.
+// the rows b < Py/2 (kernel_gen; the other rows mirror them), transform
+// them along x (row_r2c), transform the columns (y) by the parity fold and
+// keep the real or imaginary part of ky <= Py/2 per layer; then transform
+// each (kx, ky) sequence over the layers along z and keep the real or
+// imaginary part of kz <= Pz/2.
 //
 // Forward, per call (five passes through HBM; B = ncomp):
 //   A  x: row transforms of rho (R2C, row_r2c)          -> X[kx][n][y]
@@ -611,32 +612,44 @@ __global__ void __launch_bounds__(kZ2Threads, 16 / kZ2Warps)
     }
 }
 
-// Plan creation, column step: y-FFT of the kernel row transforms
-// Ehat[kx][o][b] (o < cnt layers of one component, b < py) and the real
-// (imag2 = false) or imaginary part of ky <= Py/2, stored as
-// T[(kx * jyc + ky) * nzw + j0 + o].
-template <int LOGY, int NSEQ>
-__global__ void __launch_bounds__(kVolThreads) vol_spec_y_kernel(const double2* __restrict__ ehat, int cnt,
-                                                                 int kx_count, int j0, int nzw, bool imag2,
-                                                                 double* __restrict__ T,
-                                                                 const double2* __restrict__ tw, int tw_shift) {
-    constexpr int N = 1 << LOGY, SSTR = seq_stride<double2>(N), JYC = N / 2 + 1;
+// Plan creation, column step from half rows: Ehat[kx][o][b] holds only the
+// rows b < N = Py/2 of each embedded kernel (row Py - b is row b times the
+// component's sign in y, row Py/2 is zero).  CTA (kx, r, group of NSEQ
+// layers) folds each column for ky parity r,
+//   a[m] = (x[m] + (-1)^r x[m + N]) W_Py^(m r),  x[m + N] = sign x[N - m],
+// runs the N-point FFT (bin q is ky = 2q + r) and stores the real or
+// imaginary part of ky <= Py/2 as T[(kx * jyc + ky) * nzw + j0 + o].
+template <int LOGN, int NSEQ>
+__global__ void __launch_bounds__(kVolThreads) vol_spec_y2_kernel(const double2* __restrict__ ehat, int cnt, int j0,
+                                                                  int nzw, bool imag2, bool oddv,
+                                                                  double* __restrict__ T,
+                                                                  const double2* __restrict__ tw, int tw_shift_n,
+                                                                  int tw_shift_p) {
+    constexpr int N = 1 << LOGN, SSTR = seq_stride<double2>(N), JYC = N + 1;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     double2* buf = reinterpret_cast<double2*>(smem_raw);
     const int tid = threadIdx.x;
-    const long rows = (long)kx_count * cnt;
-    const long row0 = (long)blockIdx.x * NSEQ;
-    block_fft_from<double2, LOGY, NSEQ, kVolThreads, false>(buf, SSTR, tw, tw_shift, tid, [&](int s, int m) {
-        const long k = row0 + s;
-        return k < rows ? ehat[k * N + m] : cmk<double2>(0, 0);
-    });
-    for (int e = tid; e < NSEQ * JYC; e += kVolThreads) {
-        const int s = e / JYC, ky = e - s * JYC;
-        const long k = row0 + s;
-        if (k >= rows) continue;
-        const int kx = (int)(k / cnt), o = (int)(k - (long)kx * cnt);
-        const double2 v = buf[s * SSTR + sidx<double2>(ky)];
-        T[((size_t)kx * JYC + ky) * nzw + j0 + o] = imag2 ? v.y : v.x;
+    const int kx = blockIdx.x, r = blockIdx.y, o0 = blockIdx.z * NSEQ;
+    const double sgn = oddv ? -1.0 : 1.0;
+    for (int e = tid; e < NSEQ * N; e += kVolThreads) {
+        const int sq = e / N, m = e - sq * N, o = o0 + sq;
+        double2 v = cmk<double2>(0, 0);
+        if (o < cnt) {
+            const double2* col = ehat + ((size_t)kx * cnt + o) * N;
+            const double2 x0 = col[m];
+            const double2 x1 = m ? cscale(col[N - m], sgn) : cmk<double2>(0, 0);
+            v = r ? cmul(csub(x0, x1), tw[m << tw_shift_p]) : cadd(x0, x1);
+        }
+        buf[sq * SSTR + sidx<double2>(m)] = v;
+    }
+    __syncthreads();
+    block_fft<double2, LOGN, NSEQ, kVolThreads, false>(buf, SSTR, tw, tw_shift_n, tid);
+    const int nq = r ? N / 2 : N / 2 + 1;  // the bins 2q + r <= Py/2
+    for (int e = tid; e < NSEQ * nq; e += kVolThreads) {
+        const int sq = e / nq, q = e - sq * nq, o = o0 + sq;
+        if (o >= cnt) continue;
+        const double2 z = buf[sq * SSTR + sidx<double2>(q)];
+        T[((size_t)kx * JYC + 2 * q + r) * nzw + j0 + o] = imag2 ? z.y : z.x;
     }
 }
 
@@ -800,18 +813,31 @@ cudaError_t launch_vol_z(int logz, const ZArgs& a, const void* in, void* out, co
     }
 }
 
-template <int LOGY>
-cudaError_t spec_y_launch(const void* ehat, int cnt, int kx_count, int j0, int nzw, bool imag2, double* T,
-                          const void* tw64, int log_t, cudaStream_t s) {
-    constexpr int NSEQ = rows_nseq<double2>(LOGY);
-    constexpr auto k = vol_spec_y_kernel<LOGY, NSEQ>;
-    const size_t smem = (size_t)NSEQ * seq_stride<double2>(1 << LOGY) * sizeof(double2);
+constexpr int kSpecY2Seqs = 4;
+
+template <int LOGN>
+cudaError_t spec_y2_launch(const void* ehat, int cnt, int kx_count, int j0, int nzw, bool imag2, bool oddv, double* T,
+                           const void* tw64, int log_t, cudaStream_t s) {
+    constexpr auto k = vol_spec_y2_kernel<LOGN, kSpecY2Seqs>;
+    const size_t smem = (size_t)kSpecY2Seqs * seq_stride<double2>(1 << LOGN) * sizeof(double2);
     cudaError_t e = ensure_smem_limit<k>();
     if (e != cudaSuccess) return e;
-    const long rows = (long)kx_count * cnt;
-    k<<<(unsigned)((rows + NSEQ - 1) / NSEQ), kVolThreads, smem, s>>>((const double2*)ehat, cnt, kx_count, j0, nzw,
-                                                                       imag2, T, (const double2*)tw64, log_t - LOGY);
+    const dim3 grid(kx_count, 2, (cnt + kSpecY2Seqs - 1) / kSpecY2Seqs);
+    k<<<grid, kVolThreads, smem, s>>>((const double2*)ehat, cnt, j0, nzw, imag2, oddv, T, (const double2*)tw64,
+                                      log_t - LOGN, log_t - (LOGN + 1));
     return cudaGetLastError();
+}
+
+// log_n = log2(Py / 2)
+cudaError_t launch_spec_y2(int log_n, const void* ehat, int cnt, int kx_count, int j0, int nzw, bool imag2, bool oddv,
+                           double* T, const void* tw64, int log_t, cudaStream_t s) {
+    switch (log_n) {
+#define CASE(L) \
+    case L: return spec_y2_launch<L>(ehat, cnt, kx_count, j0, nzw, imag2, oddv, T, tw64, log_t, s);
+        CASE(1) GRAV_VOL_LOG_CASES(CASE)
+#undef CASE
+        default: return cudaErrorInvalidValue;
+    }
 }
 
 template <typename RO, int LOGZ>
@@ -827,16 +853,6 @@ cudaError_t spec_z_launch(const double* T, long rows, int nz, bool imag2, bool i
     return cudaGetLastError();
 }
 
-cudaError_t launch_spec_y(int logy, const void* ehat, int cnt, int kx_count, int j0, int nzw, bool imag2, double* T,
-                          const void* tw64, int log_t, cudaStream_t s) {
-    switch (logy) {
-#define CASE(L) \
-    case L: return spec_y_launch<L>(ehat, cnt, kx_count, j0, nzw, imag2, T, tw64, log_t, s);
-        GRAV_VOL_LOG_CASES(CASE)
-#undef CASE
-        default: return cudaErrorInvalidValue;
-    }
-}
 
 template <typename RO>
 cudaError_t launch_spec_z(int logz, const double* T, long rows, int nz, bool imag2, bool imag3, double scale,
@@ -874,10 +890,11 @@ template <typename R>
 int make_spectra3(grav_plan* p) {
     const int nzw = 2 * p->nz - 1;
     const int jyc = p->py / 2 + 1, jzc = p->pz / 2 + 1;
-    // FP64 staging per chunk of layers of one component: the embedded
-    // kernels and their row transforms, bounded to about 2 GB; plus the
-    // column-step output T of one component.
-    const size_t per_layer = (size_t)p->py * p->px * sizeof(double) + (size_t)p->kx_count * p->py * 2 * sizeof(double);
+    // FP64 staging per chunk of layers of one component: the rows b < Py/2
+    // of the embedded kernels and their row transforms, bounded to about
+    // 2 GB; plus the column-step output T of one component.
+    const int hy = p->py / 2;
+    const size_t per_layer = (size_t)hy * p->px * sizeof(double) + (size_t)p->kx_count * hy * 2 * sizeof(double);
     int nzc = (int)(((size_t)2 << 30) / per_layer);
     if (nzc < 1) nzc = 1;
     if (nzc > nzw) nzc = nzw;
@@ -891,8 +908,8 @@ int make_spectra3(grav_plan* p) {
         return rc;
     }
     void *E = nullptr, *Ehat = nullptr, *T = nullptr;
-    const size_t e_bytes = (size_t)nzc * p->py * p->px * sizeof(double);
-    const size_t eh_bytes = (size_t)p->kx_count * nzc * p->py * 2 * sizeof(double);
+    const size_t e_bytes = (size_t)nzc * hy * p->px * sizeof(double);
+    const size_t eh_bytes = (size_t)p->kx_count * nzc * hy * 2 * sizeof(double);
     const size_t t_bytes = (size_t)p->kx_count * jyc * nzw * sizeof(double);
     if ((rc = dev_alloc_raw(&E, e_bytes, "kernel staging")) == GRAV_OK &&
         (rc = dev_alloc_raw(&Ehat, eh_bytes, "kernel row-transform staging")) == GRAV_OK &&
@@ -912,22 +929,21 @@ int make_spectra3(grav_plan* p) {
                 for (int j0 = 0; j0 < nzw && rc == GRAV_OK; j0 += nzc) {
                     const int j1 = j0 + nzc < nzw ? j0 + nzc : nzw;
                     const int cnt = j1 - j0;
-                    if ((ce = cudaMemsetAsync(E, 0, (size_t)cnt * p->py * p->px * sizeof(double), s)) != cudaSuccess) {
+                    if ((ce = cudaMemsetAsync(E, 0, (size_t)cnt * hy * p->px * sizeof(double), s)) != cudaSuccess) {
                         rc = cuda_fail(ce, "cudaMemsetAsync(kernel staging)");
                         break;
                     }
-                    if ((ce = launch_kernel_gen(g, 1u << c, j0, j1, 0, p->px, p->py, (double*)E, s)) != cudaSuccess) {
+                    if ((ce = launch_kernel_gen(g, 1u << c, j0, j1, 2, p->px, p->py, (double*)E, s)) != cudaSuccess) {
                         rc = cuda_fail(ce, "kernel generation launch");
                         break;
                     }
-                    if ((ce = launch_row_r2c<double>(p->log_px, (const double*)E, (size_t)p->py * p->px, (size_t)p->px,
-                                                     p->px, p->py, cnt, Ehat, p->py, tw64, p->log_t, s)) !=
-                        cudaSuccess) {
+                    if ((ce = launch_row_r2c<double>(p->log_px, (const double*)E, (size_t)hy * p->px, (size_t)p->px,
+                                                     p->px, hy, cnt, Ehat, hy, tw64, p->log_t, s)) != cudaSuccess) {
                         rc = cuda_fail(ce, "kernel row transform launch");
                         break;
                     }
-                    if ((ce = launch_spec_y(p->log_py, Ehat, cnt, p->kx_count, j0, nzw, imag2, (double*)T, tw64,
-                                            p->log_t, s)) != cudaSuccess) {
+                    if ((ce = launch_spec_y2(p->log_py - 1, Ehat, cnt, p->kx_count, j0, nzw, imag2, odd_v(c),
+                                             (double*)T, tw64, p->log_t, s)) != cudaSuccess) {
                         rc = cuda_fail(ce, "kernel column transform launch");
                         break;
                     }
