@@ -260,7 +260,8 @@ __global__ void __launch_bounds__(kRwThreads, 2)
 //   z[2m + 1] = sum_{k < 1024} (Z(k) - Z(k + 1024)) W_2048^(-k) W_1024^(-m k)
 // one 1024-point warp transform each (warp_fft1024), with Z(k) = A(k) + i B(k)
 // for the packed rows a, b and Z(k) for k > 1024 from Hermitian symmetry.
-// Persistent CTAs, one per SM.  A tile is 8 rows of one layer: two
+// Persistent CTAs, one per SM (two inputs) or two (one input, see
+// kCt1Region).  A tile is 8 rows of one layer: two
 // contiguous runs (one per parity) brought in by bulk copies on an mbarrier;
 // once every warp has read its inputs into registers, the next tile's
 // copies are issued.  Warp w handles rows 2 (w / 2), 2 (w / 2) + 1 and
@@ -273,9 +274,17 @@ constexpr size_t kCtAreaOff = 2 * kCtHalf;
 constexpr size_t kCtT2Off = kCtAreaOff + (size_t)kCtRows * kWarpFftSlot * sizeof(float2);
 constexpr size_t kCtBarOff = kCtT2Off + 1024 * sizeof(float2);
 constexpr size_t kCtSmem = kCtBarOff + 16;
+// Single input: the warps' transpose areas share the tile buffer (the tile
+// is in registers before any transform starts, and the next tile's copy is
+// issued after every transform), so two CTAs fit on an SM.
+constexpr size_t kCt1Region = (size_t)kCtRows * kWarpFftSlot * sizeof(float2);
+static_assert(kCt1Region >= kCtHalf, "one parity's tile fits in the transpose areas");
+constexpr size_t kCt1T2Off = kCt1Region;
+constexpr size_t kCt1BarOff = kCt1T2Off + 1024 * sizeof(float2);
+constexpr size_t kCt1Smem = kCt1BarOff + 16;
 
 template <bool TWO>
-__global__ void __launch_bounds__(kCtThreads, 1)
+__global__ void __launch_bounds__(kCtThreads, TWO ? 1 : 2)
     row_c2r_tiled_kernel(const float2* __restrict__ in0, const float2* __restrict__ in1, int ny, int nz,
                          float* __restrict__ out, size_t out_stride, int l_out, const float2* __restrict__ tw,
                          int log_t, size_t in_bstride, size_t out_bstride, int nbatch, int* __restrict__ err) {
@@ -283,9 +292,9 @@ __global__ void __launch_bounds__(kCtThreads, 1)
     extern __shared__ __align__(128) unsigned char smem_raw[];
     const float2* t0 = reinterpret_cast<const float2*>(smem_raw);            // [kx][8] parity 0
     const float2* t1 = reinterpret_cast<const float2*>(smem_raw + kCtHalf);  // [kx][8] parity 1
-    float2* areas = reinterpret_cast<float2*>(smem_raw + kCtAreaOff);
-    float2* t2 = reinterpret_cast<float2*>(smem_raw + kCtT2Off);
-    uint64_t* inb = reinterpret_cast<uint64_t*>(smem_raw + kCtBarOff);
+    float2* areas = reinterpret_cast<float2*>(smem_raw + (TWO ? kCtAreaOff : 0));
+    float2* t2 = reinterpret_cast<float2*>(smem_raw + (TWO ? kCtT2Off : kCt1T2Off));
+    uint64_t* inb = reinterpret_cast<uint64_t*>(smem_raw + (TWO ? kCtBarOff : kCt1BarOff));
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int ybs = ny_blocks(ny);
     const long ntiles = (long)nbatch * nz * ybs;
@@ -350,11 +359,18 @@ __global__ void __launch_bounds__(kCtThreads, 1)
             }
             return;
         }
-        if (tid == 0 && t + gridDim.x < ntiles) {
+        if (TWO && tid == 0 && t + gridDim.x < ntiles) {
             fence_proxy_async_smem();
             issue(t + gridDim.x);
         }
         warp_fft1024<true>(u, areas + warp * kWarpFftSlot, t2, lane);
+        if (!TWO) {
+            __syncthreads();  // every transform is done with the areas (the tile buffer)
+            if (tid == 0 && t + gridDim.x < ntiles) {
+                fence_proxy_async_smem();
+                issue(t + gridDim.x);
+            }
+        }
         // u[j] = z[2 m + p], m = lane + 32 bitrev5(j)
         float* oa = out + bz * out_bstride + ((size_t)n * ny + ya) * out_stride;
         float* ob = oa + out_stride;
@@ -537,7 +553,7 @@ cudaError_t c2r_tiled_launch(int grid, const void* in0, const void* in1, int ny,
     constexpr auto k = row_c2r_tiled_kernel<TWO>;
     cudaError_t e = ensure_smem_limit<k>();
     if (e != cudaSuccess) return e;
-    k<<<grid, kCtThreads, kCtSmem, s>>>((const float2*)in0, (const float2*)in1, ny, nz, out, out_stride, l_out,
+    k<<<grid, kCtThreads, TWO ? kCtSmem : kCt1Smem, s>>>((const float2*)in0, (const float2*)in1, ny, nz, out, out_stride, l_out,
                                         (const float2*)tw, log_t, b.in, b.out, b.count, err);
     return cudaGetLastError();
 }
@@ -552,7 +568,7 @@ cudaError_t launch_row_c2r_tiled(const void* in0, const void* in1, int ny, int n
     const int sms = sm_count();
     if (sms <= 0) return cudaErrorInvalidValue;
     const long ntiles = (long)b.count * nz * ny_blocks(ny);
-    const int grid = (int)std::min<long>(ntiles, sms);
+    const int grid = (int)std::min<long>(ntiles, (in1 ? 1L : 2L) * sms);
     if (grid == 0) return cudaSuccess;
     return in1 ? c2r_tiled_launch<true>(grid, in0, in1, ny, nz, out, out_stride, l_out, tw, log_t, s, b, err)
                : c2r_tiled_launch<false>(grid, in0, in1, ny, nz, out, out_stride, l_out, tw, log_t, s, b, err);
