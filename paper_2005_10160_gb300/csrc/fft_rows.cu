@@ -260,51 +260,45 @@ __global__ void __launch_bounds__(kRwThreads, 2)
 //   z[2m + 1] = sum_{k < 1024} (Z(k) - Z(k + 1024)) W_2048^(-k) W_1024^(-m k)
 // one 1024-point warp transform each (warp_fft1024), with Z(k) = A(k) + i B(k)
 // for the packed rows a, b and Z(k) for k > 1024 from Hermitian symmetry.
-// Persistent CTAs, one per SM (two inputs) or two (one input, see
-// kCt1Region).  A tile is 8 rows of one layer: two
-// contiguous runs (one per parity) brought in by bulk copies on an mbarrier;
-// once every warp has read its inputs into registers, the next tile's
-// copies are issued.  Warp w handles rows 2 (w / 2), 2 (w / 2) + 1 and
-// output parity w % 2, and stores its outputs straight to the rows.
+// Persistent CTAs, two per SM.  A tile is 8 rows of one layer: one
+// contiguous run per input (the two ky parities of the plane adjoint, or a
+// single input) brought in by a bulk copy on an mbarrier, the inputs one
+// after the other through one buffer: every warp adds its share of the
+// first input to its registers (the packed spectrum is linear in the input)
+// before the second input's copy is issued.  The warps' transpose areas
+// share that buffer, so the next tile's copy is issued once every transform
+// is done.  Warp w handles rows 2 (w / 2), 2 (w / 2) + 1 and output parity
+// w % 2, and stores its outputs straight to the rows.
 constexpr int kCtRows = 8;                         // rows per tile
 constexpr int kCtThreads = 32 * kCtRows;           // two warps per packed row pair
 constexpr int kCtKx = 1025;                        // P / 2 + 1
-constexpr size_t kCtHalf = (size_t)kCtKx * kCtRows * sizeof(float2);  // bytes of one parity's tile
-constexpr size_t kCtAreaOff = 2 * kCtHalf;
-constexpr size_t kCtT2Off = kCtAreaOff + (size_t)kCtRows * kWarpFftSlot * sizeof(float2);
-constexpr size_t kCtBarOff = kCtT2Off + 1024 * sizeof(float2);
-constexpr size_t kCtSmem = kCtBarOff + 16;
-// Single input: the warps' transpose areas share the tile buffer (the tile
-// is in registers before any transform starts, and the next tile's copy is
-// issued after every transform), so two CTAs fit on an SM.
+constexpr size_t kCtHalf = (size_t)kCtKx * kCtRows * sizeof(float2);  // bytes of one input's tile
 constexpr size_t kCt1Region = (size_t)kCtRows * kWarpFftSlot * sizeof(float2);
-static_assert(kCt1Region >= kCtHalf, "one parity's tile fits in the transpose areas");
+static_assert(kCt1Region >= kCtHalf, "one input's tile fits in the transpose areas");
 constexpr size_t kCt1T2Off = kCt1Region;
 constexpr size_t kCt1BarOff = kCt1T2Off + 1024 * sizeof(float2);
 constexpr size_t kCt1Smem = kCt1BarOff + 16;
 
 template <bool TWO>
-__global__ void __launch_bounds__(kCtThreads, TWO ? 1 : 2)
+__global__ void __launch_bounds__(kCtThreads, 2)
     row_c2r_tiled_kernel(const float2* __restrict__ in0, const float2* __restrict__ in1, int ny, int nz,
                          float* __restrict__ out, size_t out_stride, int l_out, const float2* __restrict__ tw,
                          int log_t, size_t in_bstride, size_t out_bstride, int nbatch, int* __restrict__ err) {
-    constexpr int N = 1024;
+    constexpr int N = 1024, NPH = TWO ? 2 : 1;  // inputs, brought in one after the other
     extern __shared__ __align__(128) unsigned char smem_raw[];
-    const float2* t0 = reinterpret_cast<const float2*>(smem_raw);            // [kx][8] parity 0
-    const float2* t1 = reinterpret_cast<const float2*>(smem_raw + kCtHalf);  // [kx][8] parity 1
-    float2* areas = reinterpret_cast<float2*>(smem_raw + (TWO ? kCtAreaOff : 0));
-    float2* t2 = reinterpret_cast<float2*>(smem_raw + (TWO ? kCtT2Off : kCt1T2Off));
-    uint64_t* inb = reinterpret_cast<uint64_t*>(smem_raw + (TWO ? kCtBarOff : kCt1BarOff));
+    const float2* t0 = reinterpret_cast<const float2*>(smem_raw);  // the input of this phase, [kx][8]
+    float2* areas = reinterpret_cast<float2*>(smem_raw);           // transpose areas, once t0 is read
+    float2* t2 = reinterpret_cast<float2*>(smem_raw + kCt1T2Off);
+    uint64_t* inb = reinterpret_cast<uint64_t*>(smem_raw + kCt1BarOff);
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int ybs = ny_blocks(ny);
     const long ntiles = (long)nbatch * nz * ybs;
 
-    auto issue = [&](long t) {  // thread 0: both parities' runs of tile t
+    auto issue = [&](long t, int ph) {  // thread 0: input ph's run of tile t
         const long bz = t / ((long)nz * ybs), rest = t - bz * nz * ybs;  // rest = n * ybs + yb
         const size_t off = (size_t)rest * kCtKx * kCtRows;
-        mbar_arrive_expect_tx(inb, (uint32_t)((TWO ? 2 : 1) * kCtHalf));
-        bulk_g2s(smem_raw, in0 + bz * in_bstride + off, (uint32_t)kCtHalf, inb);
-        if (TWO) bulk_g2s(smem_raw + kCtHalf, in1 + bz * in_bstride + off, (uint32_t)kCtHalf, inb);
+        mbar_arrive_expect_tx(inb, (uint32_t)kCtHalf);
+        bulk_g2s(smem_raw, (ph ? in1 : in0) + bz * in_bstride + off, (uint32_t)kCtHalf, inb);
     };
 
     if (tid == 0) {
@@ -313,63 +307,70 @@ __global__ void __launch_bounds__(kCtThreads, TWO ? 1 : 2)
     }
     for (int e = tid; e < N; e += kCtThreads) t2[e] = tw[(((e >> 5) * (e & 31)) & (N - 1)) << (log_t - 10)];
     __syncthreads();
-    if (tid == 0 && blockIdx.x < ntiles) issue(blockIdx.x);
+    if (tid == 0 && blockIdx.x < ntiles) issue(blockIdx.x, 0);
 
     const int sq = warp >> 1, p = warp & 1;
     // odd outputs: W_2048^(-k) with k = 32 n1 + lane = W_64^(-n1) W_2048^(-lane)
     const float2 wl = cconj(tw[lane << (log_t - 11)]);
-    int it = 0;
-    for (long t = blockIdx.x; t < ntiles; t += gridDim.x, ++it) {
+    uint32_t waits = 0;  // completed phases of inb
+    for (long t = blockIdx.x; t < ntiles; t += gridDim.x) {
         const long bz = t / ((long)nz * ybs), rest = t - bz * nz * ybs;
         const int n = (int)(rest / ybs), yb = (int)(rest - (long)n * ybs);
         const int ya = yb * kCtRows + 2 * sq;
-        const bool ok = mbar_wait_bounded(inb, (uint32_t)(it & 1), kWaitLimitNs);
-        const bool ha = ok && ya < ny, hb = ok && ya + 1 < ny;
-        // packed spectrum Z(k) = A(k) + i B(k) of rows ya, ya + 1 at kx (both parities summed)
-        auto zk = [&](int kx) {
-            const int pos = 2 * ((sq + (kx >> 1)) & 3);  // row pair sq's 16-byte position in the run
-            const float4 v0 = *reinterpret_cast<const float4*>(t0 + kx * kCtRows + pos);
-            const float4 v1 = TWO ? *reinterpret_cast<const float4*>(t1 + kx * kCtRows + pos)
-                                  : make_float4(0.f, 0.f, 0.f, 0.f);
-            float2 A = make_float2(v0.x + v1.x, v0.y + v1.y), B = make_float2(v0.z + v1.z, v0.w + v1.w);
-            if (!ha) A = make_float2(0.f, 0.f);
-            if (!hb) B = make_float2(0.f, 0.f);
-            if (kx == 0 || kx == kCtKx - 1) A.y = B.y = 0.f;  // real DC and Nyquist
-            return make_float4(A.x, A.y, B.x, B.y);
-        };
+        // v[n1] = Z(k) +- Z(k + 1024) (output parity p), k = 32 n1 + lane, for the
+        // packed spectrum Z = A + i B of rows ya, ya + 1: linear in the input, so
+        // each input's share is added in turn
         float2 u[32];
 #pragma unroll
-        for (int n1 = 0; n1 < 32; ++n1) {
-            const int k = 32 * n1 + lane;
-            const float4 a1 = zk(k);
-            const float2 z1 = make_float2(a1.x - a1.w, a1.y + a1.z);  // A + i B
-            const float4 a2 = zk(N - k);                                // k = 0: the Nyquist bin itself
-            // Z(k + 1024) = conj A(1024 - k) + i conj B(1024 - k) (k > 0), A + i B at the Nyquist bin (k = 0)
-            const float2 z2 = k ? make_float2(a2.x + a2.w, a2.z - a2.y) : make_float2(a2.x - a2.w, a2.y + a2.z);
-            float2 v = p ? make_float2(z1.x - z2.x, z1.y - z2.y) : make_float2(z1.x + z2.x, z1.y + z2.y);
-            if (p) v = cmul(tw64(v, -n1), wl);
-            u[n1] = v;
-        }
-        if (__syncthreads_or(!ok)) {
-            // a copy did not land in time: record it, let the copy land
-            // (bounded) before the shared memory is released, and leave
-            if (tid == 0) {
-                atomicExch(err, 1);
-                mbar_wait_bounded(inb, (uint32_t)(it & 1), kWaitLimitNs);
+        for (int n1 = 0; n1 < 32; ++n1) u[n1] = make_float2(0.f, 0.f);
+#pragma unroll 1
+        for (int ph = 0; ph < NPH; ++ph) {
+            const bool ok = mbar_wait_bounded(inb, waits & 1u, kWaitLimitNs);
+            ++waits;
+            const bool ha = ok && ya < ny, hb = ok && ya + 1 < ny;
+            auto zk = [&](int kx) {  // (A, B) of this input at kx
+                const int pos = 2 * ((sq + (kx >> 1)) & 3);  // row pair sq's 16-byte position in the run
+                const float4 v0 = *reinterpret_cast<const float4*>(t0 + kx * kCtRows + pos);
+                float2 A = make_float2(v0.x, v0.y), B = make_float2(v0.z, v0.w);
+                if (!ha) A = make_float2(0.f, 0.f);
+                if (!hb) B = make_float2(0.f, 0.f);
+                if (kx == 0 || kx == kCtKx - 1) A.y = B.y = 0.f;  // real DC and Nyquist
+                return make_float4(A.x, A.y, B.x, B.y);
+            };
+#pragma unroll
+            for (int n1 = 0; n1 < 32; ++n1) {
+                const int k = 32 * n1 + lane;
+                const float4 a1 = zk(k);
+                const float2 z1 = make_float2(a1.x - a1.w, a1.y + a1.z);  // A + i B
+                const float4 a2 = zk(N - k);                                // k = 0: the Nyquist bin itself
+                // Z(k + 1024) = conj A(1024 - k) + i conj B(1024 - k) (k > 0), A + i B at the Nyquist bin (k = 0)
+                const float2 z2 = k ? make_float2(a2.x + a2.w, a2.z - a2.y) : make_float2(a2.x - a2.w, a2.y + a2.z);
+                const float2 v = p ? make_float2(z1.x - z2.x, z1.y - z2.y) : make_float2(z1.x + z2.x, z1.y + z2.y);
+                u[n1] = make_float2(u[n1].x + v.x, u[n1].y + v.y);
             }
-            return;
+            if (__syncthreads_or(!ok)) {
+                // a copy did not land in time: record it, let the copy land
+                // (bounded) before the shared memory is released, and leave
+                if (tid == 0) {
+                    atomicExch(err, 1);
+                    mbar_wait_bounded(inb, (waits - 1) & 1u, kWaitLimitNs);
+                }
+                return;
+            }
+            if (ph + 1 < NPH && tid == 0) {  // every warp has read this input: the next one
+                fence_proxy_async_smem();
+                issue(t, ph + 1);
+            }
         }
-        if (TWO && tid == 0 && t + gridDim.x < ntiles) {
-            fence_proxy_async_smem();
-            issue(t + gridDim.x);
+        if (p) {
+#pragma unroll
+            for (int n1 = 0; n1 < 32; ++n1) u[n1] = cmul(tw64(u[n1], -n1), wl);
         }
         warp_fft1024<true>(u, areas + warp * kWarpFftSlot, t2, lane);
-        if (!TWO) {
-            __syncthreads();  // every transform is done with the areas (the tile buffer)
-            if (tid == 0 && t + gridDim.x < ntiles) {
-                fence_proxy_async_smem();
-                issue(t + gridDim.x);
-            }
+        __syncthreads();  // every transform is done with the areas (the tile buffer)
+        if (tid == 0 && t + gridDim.x < ntiles) {
+            fence_proxy_async_smem();
+            issue(t + gridDim.x, 0);
         }
         // u[j] = z[2 m + p], m = lane + 32 bitrev5(j)
         float* oa = out + bz * out_bstride + ((size_t)n * ny + ya) * out_stride;
@@ -553,7 +554,7 @@ cudaError_t c2r_tiled_launch(int grid, const void* in0, const void* in1, int ny,
     constexpr auto k = row_c2r_tiled_kernel<TWO>;
     cudaError_t e = ensure_smem_limit<k>();
     if (e != cudaSuccess) return e;
-    k<<<grid, kCtThreads, TWO ? kCtSmem : kCt1Smem, s>>>((const float2*)in0, (const float2*)in1, ny, nz, out, out_stride, l_out,
+    k<<<grid, kCtThreads, kCt1Smem, s>>>((const float2*)in0, (const float2*)in1, ny, nz, out, out_stride, l_out,
                                         (const float2*)tw, log_t, b.in, b.out, b.count, err);
     return cudaGetLastError();
 }
@@ -568,7 +569,7 @@ cudaError_t launch_row_c2r_tiled(const void* in0, const void* in1, int ny, int n
     const int sms = sm_count();
     if (sms <= 0) return cudaErrorInvalidValue;
     const long ntiles = (long)b.count * nz * ny_blocks(ny);
-    const int grid = (int)std::min<long>(ntiles, (in1 ? 1L : 2L) * sms);
+    const int grid = (int)std::min<long>(ntiles, 2L * sms);
     if (grid == 0) return cudaSuccess;
     return in1 ? c2r_tiled_launch<true>(grid, in0, in1, ny, nz, out, out_stride, l_out, tw, log_t, s, b, err)
                : c2r_tiled_launch<false>(grid, in0, in1, ny, nz, out, out_stride, l_out, tw, log_t, s, b, err);
