@@ -476,26 +476,30 @@ __global__ void __launch_bounds__(kZ2Threads, 16 / kZ2Warps)
     for (int e = tid; e < 256; e += kZ2Threads) tab[e] = tw[((e >> 4) * (e & 15)) << a.tw_shift];
 
     // nz rows of the tile's 16 columns (zero beyond py) into a staging tile
+    // A thread moves column ti = tid % kZ2Ti of the tile, rows tr0, tr0 +
+    // kZ2Rs, ...: its shared and global addresses advance by fixed strides.
+    constexpr int kZ2Rs = kZ2Threads / kZ2Ti;  // rows per pass of the CTA
+    const int ti = tid % kZ2Ti, tr0 = tid / kZ2Ti;
+    const bool ti_ok = ky0 + ti < py;
+    const size_t gstep = (size_t)kZ2Rs * py;
     auto load_tile = [&](float2* st, const float2* src) {
-        for (int e = tid; e < kZ2Ti * nz; e += kZ2Threads) {
-            const int n = e / kZ2Ti, i = e % kZ2Ti;
-            st[n * kZ2Str + i] = (ky0 + i < py) ? src[(size_t)n * py + ky0 + i] : make_float2(0.f, 0.f);
-        }
+        float2* sp = st + tr0 * kZ2Str + ti;
+        const float2* gp = src + (size_t)tr0 * py + ky0 + ti;
+        for (int n = tr0; n < nz; n += kZ2Rs, sp += kZ2Rs * kZ2Str, gp += gstep)
+            *sp = ti_ok ? *gp : make_float2(0.f, 0.f);
     };
     // the same by per-thread asynchronous copies (one group per call)
     auto issue_tile = [&](float2* st, const float2* src) {
-        for (int e = tid; e < kZ2Ti * nz; e += kZ2Threads) {
-            const int n = e / kZ2Ti, i = e % kZ2Ti;
-            const bool ok = ky0 + i < py;
-            async8_g2s(st + n * kZ2Str + i, ok ? src + (size_t)n * py + ky0 + i : src, ok);
-        }
+        float2* sp = st + tr0 * kZ2Str + ti;
+        const float2* gp = src + (size_t)tr0 * py + (ti_ok ? ky0 + ti : 0);
+        for (int n = tr0; n < nz; n += kZ2Rs, sp += kZ2Rs * kZ2Str, gp += gstep) async8_g2s(sp, gp, ti_ok);
         async8_commit();
     };
     auto store_tile = [&](const float2* st, float2* dst) {
-        for (int e = tid; e < kZ2Ti * nz; e += kZ2Threads) {
-            const int t = e / kZ2Ti, i = e % kZ2Ti;
-            if (ky0 + i < py) dst[(size_t)t * py + ky0 + i] = st[t * kZ2Str + i];
-        }
+        if (!ti_ok) return;
+        const float2* sp = st + tr0 * kZ2Str + ti;
+        float2* gp = dst + (size_t)tr0 * py + ky0 + ti;
+        for (int t = tr0; t < nz; t += kZ2Rs, sp += kZ2Rs * kZ2Str, gp += gstep) *gp = *sp;
     };
     // forward transform of this lane's column from a staging tile
     auto fwd_fft = [&](const float2* st, float2 (&u)[16]) {
@@ -543,15 +547,20 @@ __global__ void __launch_bounds__(kZ2Threads, 16 / kZ2Warps)
     };
     // spectrum of slot c at (ky, kz = q + 16 bitrev4(j)) as the real v with
     // S = v or S = i v
+    const float* spec_lane = spec3 + ((size_t)kx * a.jyc + jy) * a.jzc;  // slot 0
+    const size_t spec_slot = (size_t)a.kx_count * a.jyc * a.jzc;
     auto load_spec = [&](int c, float (&v)[16]) {
-        const float* base = spec3 + (((size_t)c * a.kx_count + kx) * a.jyc + jy) * a.jzc;
-        const bool ov = (a.oddv_mask >> c) & 1u, ow = (a.oddw_mask >> c) & 1u;
+        const float* base = spec_lane + c * spec_slot;
+        // the sign of S(ky, kz) against the stored value: flipped by the
+        // y parity for ky > Py/2 and by the w parity for kz > Pz/2
+        const bool s_lo = fy && ((a.oddv_mask >> c) & 1u);
+        const bool s_hi = s_lo != (((a.oddw_mask >> c) & 1u) != 0);
 #pragma unroll
         for (int j = 0; j < 16; ++j) {
             const int kz = q + 16 * bitrev4(j);
             const bool fz = kz > 128;
             const float val = kyok ? __ldg(base + (fz ? 256 - kz : kz)) : 0.f;
-            v[j] = ((fy && ov) != (fz && ow)) ? -val : val;
+            v[j] = (fz ? s_hi : s_lo) ? -val : val;
         }
     };
 
@@ -564,11 +573,14 @@ __global__ void __launch_bounds__(kZ2Threads, 16 / kZ2Warps)
         float v[16];
         load_spec(0, v);
         for (int c = 0; c < a.ncomp; ++c) {
-            const bool imag = (a.imag3_mask >> c) & 1u;
             float2 g[16];
+            if ((a.imag3_mask >> c) & 1u) {  // S = i v
 #pragma unroll
-            for (int j = 0; j < 16; ++j)
-                g[j] = imag ? make_float2(-v[j] * X[j].y, v[j] * X[j].x) : make_float2(v[j] * X[j].x, v[j] * X[j].y);
+                for (int j = 0; j < 16; ++j) g[j] = make_float2(-v[j] * X[j].y, v[j] * X[j].x);
+            } else {
+#pragma unroll
+                for (int j = 0; j < 16; ++j) g[j] = make_float2(v[j] * X[j].x, v[j] * X[j].y);
+            }
             if (c + 1 < a.ncomp) load_spec(c + 1, v);  // in flight during the transform
             inv_fft(g);
             // staging tile c % 2: its last reader (the store of component
@@ -598,11 +610,13 @@ __global__ void __launch_bounds__(kZ2Threads, 16 / kZ2Warps)
                 issue_tile(stage + ((c + 1) & 1) * kZ2Stage, in + ((size_t)kx * a.ncomp + c + 1) * nz * py);
             float2 f[16];
             fwd_fft(st, f);
-            const bool imag = (a.imag3_mask >> c) & 1u;
+            if ((a.imag3_mask >> c) & 1u) {  // conj(S) f with S = i v
 #pragma unroll
-            for (int j = 0; j < 16; ++j)  // conj(S) f: S = v or S = i v
-                acc[j] = imag ? make_float2(acc[j].x + v[j] * f[j].y, acc[j].y - v[j] * f[j].x)
-                              : make_float2(acc[j].x + v[j] * f[j].x, acc[j].y + v[j] * f[j].y);
+                for (int j = 0; j < 16; ++j) acc[j] = make_float2(acc[j].x + v[j] * f[j].y, acc[j].y - v[j] * f[j].x);
+            } else {  // S = v
+#pragma unroll
+                for (int j = 0; j < 16; ++j) acc[j] = make_float2(acc[j].x + v[j] * f[j].x, acc[j].y + v[j] * f[j].y);
+            }
         }
         inv_fft(acc);
         float2* st = stage + (a.ncomp & 1) * kZ2Stage;  // not the tile the last component read
