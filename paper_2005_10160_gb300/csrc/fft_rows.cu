@@ -13,6 +13,7 @@
 // by Hermitian symmetry, two rows are packed as A + i B, inverse FFT'd, and
 // the first l_out points of each row are kept (the crop back to the
 // stations).
+#include <climits>
 #include <algorithm>
 
 #include "async_copy.cuh"
@@ -151,14 +152,15 @@ __global__ void __launch_bounds__(kRwThreads, 2)
     float2* t2 = reinterpret_cast<float2*>(smem_raw + kRwT2Off);      // W_1024^(k1 n2) at [k1][n2]
     uint64_t* inb = reinterpret_cast<uint64_t*>(smem_raw + kRwBarOff);
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    const int rbs = (I + kRwRows - 1) / kRwRows;  // row blocks per layer
-    const long ntiles = (long)nbatch * O * rbs;
+    // tile t = (bz O + o) rbs + rb, in 32 bits (the launch checks the count)
+    const unsigned rbs = (unsigned)(I + kRwRows - 1) / kRwRows;  // row blocks per layer
+    const unsigned ntiles = (unsigned)nbatch * (unsigned)O * rbs;
 
     // bulk copies of tile t's rows (thread 0)
-    auto issue = [&](long t) {
-        const int rb = (int)(t % rbs);
-        const long rest = t / rbs;
-        const int o = (int)(rest % O), bz = (int)(rest / O);
+    auto issue = [&](unsigned t) {
+        const unsigned rest = t / rbs;
+        const int rb = (int)(t - rest * rbs);
+        const int bz = (int)(rest / (unsigned)O), o = (int)(rest - (unsigned)bz * (unsigned)O);
         const int i0 = rb * kRwRows, nrows = min(kRwRows, I - i0);
         const uint32_t row_bytes = (uint32_t)l_in * sizeof(float);
         const float* src = in + bz * in_bstride + (size_t)o * in_ostride + (size_t)i0 * in_istride;
@@ -178,10 +180,10 @@ __global__ void __launch_bounds__(kRwThreads, 2)
     // odd outputs: z[x] W_2048^x with x = 32 n1 + lane, W_2048^x = W_64^n1 W_2048^lane
     const float2 wl = tw[lane << (log_t - 11)];
     int it = 0;
-    for (long t = blockIdx.x; t < ntiles; t += gridDim.x, ++it) {
-        const int rb = (int)(t % rbs);
-        const long rest = t / rbs;
-        const int o = (int)(rest % O), bz = (int)(rest / O);
+    for (unsigned t = blockIdx.x; t < ntiles; t += gridDim.x, ++it) {
+        const unsigned rest = t / rbs;
+        const int rb = (int)(t - rest * rbs);
+        const int bz = (int)(rest / (unsigned)O), o = (int)(rest - (unsigned)bz * (unsigned)O);
         const int ib = rb * kRwRows;
         const bool ok = mbar_wait_bounded(inb, (uint32_t)(it & 1), kWaitLimitNs);
         const int i0 = ib + 2 * sq;
@@ -292,10 +294,12 @@ __global__ void __launch_bounds__(kCtThreads, 2)
     uint64_t* inb = reinterpret_cast<uint64_t*>(smem_raw + kCt1BarOff);
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int ybs = ny_blocks(ny);
-    const long ntiles = (long)nbatch * nz * ybs;
+    // tile t = (bz nz + n) ybs + yb, in 32 bits (the launch checks the count)
+    const unsigned per_b = (unsigned)nz * (unsigned)ybs;
+    const unsigned ntiles = (unsigned)nbatch * per_b;
 
-    auto issue = [&](long t, int ph) {  // thread 0: input ph's run of tile t
-        const long bz = t / ((long)nz * ybs), rest = t - bz * nz * ybs;  // rest = n * ybs + yb
+    auto issue = [&](unsigned t, int ph) {  // thread 0: input ph's run of tile t
+        const unsigned bz = t / per_b, rest = t - bz * per_b;  // rest = n * ybs + yb
         const size_t off = (size_t)rest * kCtKx * kCtRows;
         mbar_arrive_expect_tx(inb, (uint32_t)kCtHalf);
         bulk_g2s(smem_raw, (ph ? in1 : in0) + bz * in_bstride + off, (uint32_t)kCtHalf, inb);
@@ -313,9 +317,9 @@ __global__ void __launch_bounds__(kCtThreads, 2)
     // odd outputs: W_2048^(-k) with k = 32 n1 + lane = W_64^(-n1) W_2048^(-lane)
     const float2 wl = cconj(tw[lane << (log_t - 11)]);
     uint32_t waits = 0;  // completed phases of inb
-    for (long t = blockIdx.x; t < ntiles; t += gridDim.x) {
-        const long bz = t / ((long)nz * ybs), rest = t - bz * nz * ybs;
-        const int n = (int)(rest / ybs), yb = (int)(rest - (long)n * ybs);
+    for (unsigned t = blockIdx.x; t < ntiles; t += gridDim.x) {
+        const unsigned bz = t / per_b, rest = t - bz * per_b;
+        const int n = (int)(rest / (unsigned)ybs), yb = (int)(rest - (unsigned)n * (unsigned)ybs);
         const int ya = yb * kCtRows + 2 * sq;
         // v[n1] = Z(k) +- Z(k + 1024) (output parity p), k = 32 n1 + lane, for the
         // packed spectrum Z = A + i B of rows ya, ya + 1: linear in the input, so
@@ -479,14 +483,15 @@ cudaError_t r2c_impl(const R* in, size_t in_ostride, size_t in_istride, int l_in
         // 2048-point float rows, at most 1024 nonzero, 16-byte aligned rows:
         // two warp transforms per row pair, rows staged by bulk copies
         const int sms = sm_count();
+        const long ntiles = (long)b.count * O * ((I + kRwRows - 1) / kRwRows);
         const bool fits = err && sms > 0 && l_in <= kRwPitch && l_in % 4 == 0 && in_istride % 4 == 0 &&
                           in_ostride % 4 == 0 && b.in % 4 == 0 && (reinterpret_cast<uintptr_t>(in) & 15) == 0 &&
-                          i_pad % 2 == 0 && b.out % 2 == 0 && (reinterpret_cast<uintptr_t>(out) & 15) == 0;
+                          i_pad % 2 == 0 && b.out % 2 == 0 && (reinterpret_cast<uintptr_t>(out) & 15) == 0 &&
+                          ntiles <= INT_MAX;  // the kernel counts tiles in 32 bits
         if (fits) {
             constexpr auto k = row_r2c_warp_kernel;
             cudaError_t e = ensure_smem_limit<k>();
             if (e != cudaSuccess) return e;
-            const long ntiles = (long)b.count * O * ((I + kRwRows - 1) / kRwRows);
             const int grid = (int)std::min<long>(ntiles, 2L * sms);
             if (grid == 0) return cudaSuccess;
             k<<<grid, kRwThreads, kRwSmem, s>>>(in, in_ostride, in_istride, l_in, I, O, (float2*)out, i_pad,
@@ -569,6 +574,7 @@ cudaError_t launch_row_c2r_tiled(const void* in0, const void* in1, int ny, int n
     const int sms = sm_count();
     if (sms <= 0) return cudaErrorInvalidValue;
     const long ntiles = (long)b.count * nz * ny_blocks(ny);
+    if (ntiles > INT_MAX) return cudaErrorInvalidValue;  // the kernel counts tiles in 32 bits
     const int grid = (int)std::min<long>(ntiles, 2L * sms);
     if (grid == 0) return cudaSuccess;
     return in1 ? c2r_tiled_launch<true>(grid, in0, in1, ny, nz, out, out_stride, l_out, tw, log_t, s, b, err)

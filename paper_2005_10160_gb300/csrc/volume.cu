@@ -233,9 +233,9 @@ __global__ void __launch_bounds__(kYwThreads, 2)
     float2* tr = areas + warp * kYwArea;
     const int kxg = (kx_count + kYwRows - 1) / kYwRows;
     const int ybs = (ny + 7) >> 3;
-    const long groups = (long)kxg * R;
-    for (long g = blockIdx.x; g < groups; g += gridDim.x) {
-        const int r = (int)(g / kxg), kx0 = (int)(g - (long)r * kxg) * kYwRows;
+    const unsigned groups = (unsigned)kxg * (unsigned)R;  // at most 257 x 4608
+    for (unsigned g = blockIdx.x; g < groups; g += gridDim.x) {
+        const int r = (int)(g / (unsigned)kxg), kx0 = (int)(g - (unsigned)r * (unsigned)kxg) * kYwRows;
         const int kx = kx0 + sq;
         const bool ok = kx < kx_count;
         const float2* src = in + ((size_t)(ok ? kx : 0) * R + r) * 2048 + p;
