@@ -431,12 +431,18 @@ __global__ void __launch_bounds__(NT, 2) row_c2r_kernel(const typename cplx<R>::
     __syncthreads();
     block_fft<C, LOGP, NSEQ, NT, true>(buf, SSTR, tw, tw_shift, tid);
 
-    for (int e = tid; e < NSEQ * l_out; e += NT) {
-        const int s = e / l_out, x = e - s * l_out;
+#pragma unroll
+    for (int s = 0; s < NSEQ; ++s) {
         const int i0 = i_base + 2 * s, i1 = i0 + 1;
-        const C z = buf[s * SSTR + sidx<C>(x)];
-        if (i0 < I) out[((size_t)o * I + i0) * out_stride + x] = z.x;
-        if (i1 < I) out[((size_t)o * I + i1) * out_stride + x] = z.y;
+        if (i0 >= I) break;
+        R* oa = out + ((size_t)o * I + i0) * out_stride;
+        R* ob = oa + out_stride;
+        const C* bs = buf + s * SSTR;
+        for (int x = tid; x < l_out; x += NT) {
+            const C z = bs[sidx<C>(x)];
+            oa[x] = z.x;
+            if (i1 < I) ob[x] = z.y;
+        }
     }
 }
 

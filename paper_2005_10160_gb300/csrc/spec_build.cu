@@ -56,18 +56,22 @@ __global__ void __launch_bounds__(NT) spec_extract_kernel(const double2* __restr
     block_fft<double2, LOGN, NSEQ, NT, false>(buf, SSTR, tw, tw_shift_n, tid);
 
     const int nvals = (r == 0) ? J + 1 : J;
-    for (int e = tid; e < NSEQ * jp; e += NT) {
-        const int sq = e / jp, q = e - sq * jp, o = o0 + sq;
-        if (o >= O) continue;
+#pragma unroll
+    for (int sq = 0; sq < NSEQ; ++sq) {
+        const int o = o0 + sq;
+        if (o >= O) break;
         const int slot = o / nzc, n = n0 + (o - slot * nzc);
         const bool imag = (imag_mask >> slot) & 1u;
-        double val = 0.0;
-        if (q < nvals) {
-            const int k = (q == J) ? N / 2 : q;
-            const double2 z = buf[sq * SSTR + sidx<double2>(k)];
-            val = (imag ? z.y : z.x) * scale;
+        RO* dst = spec + (size_t)((size_t)(r * kx_count + kx) * nz + n) * ncomp * jp + (size_t)slot * jp;
+        for (int q = tid; q < jp; q += NT) {
+            double val = 0.0;
+            if (q < nvals) {
+                const int k = (q == J) ? N / 2 : q;
+                const double2 z = buf[sq * SSTR + sidx<double2>(k)];
+                val = (imag ? z.y : z.x) * scale;
+            }
+            dst[q] = (RO)val;
         }
-        spec[((size_t)((size_t)(r * kx_count + kx) * nz + n) * ncomp + slot) * jp + q] = (RO)val;
     }
 }
 

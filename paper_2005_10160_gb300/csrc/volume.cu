@@ -107,10 +107,13 @@ __global__ void __launch_bounds__(kVolThreads) vol_rows_kernel(const C* __restri
         const long k = row0 + s;
         return (k < rows && m < l_in) ? in[k * in_stride + m] : cmk<C>(0, 0);
     });
-    for (int e = tid; e < NSEQ * l_out; e += kVolThreads) {
-        const int s = e / l_out, m = e - s * l_out;
+#pragma unroll
+    for (int s = 0; s < NSEQ; ++s) {
         const long k = row0 + s;
-        if (k < rows) out[k * out_stride + m] = buf[s * SSTR + sidx<C>(m)];
+        if (k >= rows) break;
+        C* dst = out + k * out_stride;
+        const C* bs = buf + s * SSTR;
+        for (int m = tid; m < l_out; m += kVolThreads) dst[m] = bs[sidx<C>(m)];
     }
 }
 
@@ -659,11 +662,14 @@ __global__ void __launch_bounds__(kVolThreads) vol_spec_y2_kernel(const double2*
     __syncthreads();
     block_fft<double2, LOGN, NSEQ, kVolThreads, false>(buf, SSTR, tw, tw_shift_n, tid);
     const int nq = r ? N / 2 : N / 2 + 1;  // the bins 2q + r <= Py/2
-    for (int e = tid; e < NSEQ * nq; e += kVolThreads) {
-        const int sq = e / nq, q = e - sq * nq, o = o0 + sq;
-        if (o >= cnt) continue;
-        const double2 z = buf[sq * SSTR + sidx<double2>(q)];
-        T[((size_t)kx * JYC + 2 * q + r) * nzw + j0 + o] = imag2 ? z.y : z.x;
+#pragma unroll
+    for (int sq = 0; sq < NSEQ; ++sq) {
+        const int o = o0 + sq;
+        if (o >= cnt) break;
+        for (int q = tid; q < nq; q += kVolThreads) {
+            const double2 z = buf[sq * SSTR + sidx<double2>(q)];
+            T[((size_t)kx * JYC + 2 * q + r) * nzw + j0 + o] = imag2 ? z.y : z.x;
+        }
     }
 }
 
