@@ -12,6 +12,7 @@ import numpy as np
 import pytest
 import torch
 
+import golden_data
 from paper_2005_10160_gb300 import capi, workloads as W
 from paper_2005_10160_gb300.plan import Plan, kernel_values
 
@@ -143,15 +144,18 @@ def test_component_subsets(gravlib, orc, comps):
 
 
 def test_paper_cube_model(gravlib, orc):
-    """Sec. 3.1: a 300 m cube 500-800 m deep (+300 kg/m^3) under 40x40
-    stations at 50 m spacing, 50 m up.  The fast forward agrees with the
-    exact single-prism field to about 13 orders of magnitude (Fig. 7)."""
+    """Sec. 3.1 (tests/golden/sec3_1_cube_model.txt): a 300 m cube 500-800 m
+    deep (+300 kg/m^3) under 40x40 stations at 50 m spacing, 50 m up.  The
+    paper reads its fast forward's residual 13 orders of magnitude below the
+    field off Figs. 6 and 7; the FP64 path here agrees with the exact
+    single-prism field to one order of that (relative L2 per component)."""
+    claim = golden_data.load("sec3_1_cube_model.txt")["residual_orders"]
     mesh, rho, boxes = W.cube40()
     got = run_forward(mesh.tuple(), ALL7, rho, fp64=True)
     l0, l1, m0, m1, n0, n1, d = boxes[0]
     ref = orc.box_field(mesh.tuple(), ALL7, (l0, l1, m0, m1, n0, n1), d).reshape(7, mesh.ny, mesh.nx)
     err = rel_errors(got, ref, ALL7)
-    assert np.all(err <= 1e-12), err
+    assert np.all(err <= 10.0 ** (1 - claim)), err
     got32 = run_forward(mesh.tuple(), ALL7, rho.astype(np.float32), fp64=False)
     assert np.all(rel_errors(got32, ref, ALL7) <= TOL32)
     # element-wise, in mGal (gz) and Eotvos (gradients), against each component's

@@ -11,6 +11,7 @@ in the oracle fails at least one of them.
 import numpy as np
 import pytest
 
+import golden_data
 from quadrature import point_mass, prism_quadrature
 from paper_2005_10160_gb300 import workloads as W
 
@@ -47,7 +48,10 @@ def test_paper_cube_matches_quadrature(orc, station):
     a length).  The paper reports its fast algorithm 13 orders of magnitude
     below the fields it computes, so the reference it is compared with must be
     exact to well beyond that."""
-    box = (-150.0, 150.0, -150.0, 150.0, 500.0, 800.0)
+    g = golden_data.load("sec3_1_cube_model.txt")
+    half = 0.5 * g["cube_size"]
+    box = (-half, half, -half, half, g["cube_top"], g["cube_bottom"])
+    assert station[2] == -g["station_height"]
     ref = prism_quadrature(station, box, nsub=8, order=16)
     got = orc.prism(station, box)
     first, second = [0, 7, 8], [1, 2, 3, 4, 5, 6]

@@ -5,6 +5,7 @@ correlation length, and the Sec. 3.1 cube sits where the paper puts it."""
 import numpy as np
 import pytest
 
+import golden_data
 from paper_2005_10160_gb300 import workloads as W
 
 
@@ -59,17 +60,24 @@ def test_random_field_moments_and_correlation_length():
 
 
 def test_cube40_is_the_sec31_model():
-    """300 m cube, top 500 m and bottom 800 m below the ground, +300 kg/m^3,
+    """The model as Sec. 3.1 prints it (tests/golden/sec3_1_cube_model.txt):
+    300 m cube, top 500 m and bottom 800 m below the ground, +300 kg/m^3,
     centred under the middle of the 40 x 40 station grid (50 m spacing), with
-    the stations 50 m above the ground."""
+    the stations 50 m above the ground, on 40 x 40 x 20 = 32000 cells."""
+    g = golden_data.load("sec3_1_cube_model.txt")
     mesh, rho, [box] = W.cube40()
     l0, l1, m0, m1, n0, n1, d = box
-    assert (mesh.dx, mesh.dy, mesh.dz, mesh.h) == (50.0, 50.0, 50.0, 50.0)
-    assert ((l1 - l0) * mesh.dx, (m1 - m0) * mesh.dy, (n1 - n0) * mesh.dz) == (300.0, 300.0, 300.0)
-    assert (n0 * mesh.dz, n1 * mesh.dz, d) == (500.0, 800.0, 300.0)
+    assert (mesh.nx, mesh.ny, mesh.nz) == (g["mesh_nx"], g["mesh_ny"], g["mesh_nz"])
+    assert mesh.nx * mesh.ny * mesh.nz == g["cells"]
+    assert (mesh.nx, mesh.ny) == (g["stations_x"], g["stations_y"]) and mesh.nx * mesh.ny == g["stations"]
+    assert (mesh.dx, mesh.dy, mesh.h) == (g["station_spacing"], g["station_spacing"], g["station_height"])
+    side = g["cube_size"]
+    assert ((l1 - l0) * mesh.dx, (m1 - m0) * mesh.dy, (n1 - n0) * mesh.dz) == (side, side, side)
+    assert (n0 * mesh.dz, n1 * mesh.dz, d) == (g["cube_top"], g["cube_bottom"], g["cube_density"])
+    assert mesh.nz * mesh.dz >= g["cube_bottom"]
     centre = 0.5 * mesh.nx * mesh.dx  # middle of the stations (p + 1/2) dx, p < 40
     assert 0.5 * (l0 + l1) * mesh.dx == centre and 0.5 * (m0 + m1) * mesh.dy == centre
-    assert np.count_nonzero(rho) == 6 * 6 * 6
+    assert np.count_nonzero(rho) == (side / mesh.dx) ** 3
 
 
 def test_station_subset_holds_corners_and_centre():
