@@ -191,6 +191,7 @@ __global__ void __launch_bounds__(kRwThreads, 2)
         const float* ra = sin + (2 * sq) * kRwPitch;
         const float* rbp = ra + kRwPitch;
         float2 u[32];
+        // all of the tile's loads first, the odd-output fold factor after
 #pragma unroll
         for (int n1 = 0; n1 < 32; ++n1) {
             const int x = 32 * n1 + lane;
@@ -198,9 +199,12 @@ __global__ void __launch_bounds__(kRwThreads, 2)
             if (x < l_in) {
                 if (ha) v.x = ra[x];
                 if (hb) v.y = rbp[x];
-                if (p) v = cmul(tw64(v, n1), wl);
             }
             u[n1] = v;
+        }
+        if (p) {
+#pragma unroll
+            for (int n1 = 0; n1 < 32; ++n1) u[n1] = cmul(tw64(u[n1], n1), wl);
         }
         if (__syncthreads_or(!ok)) {
             // a copy did not land in time: record it, let the copy land
@@ -234,6 +238,7 @@ __global__ void __launch_bounds__(kRwThreads, 2)
                 const bool pair = j0 + 1 < I;
                 const size_t dstep = (size_t)KSTEP * O * i_pad;
                 float2* dst = out + bz * out_bstride + ((size_t)kx0 * O + o) * i_pad + j0;
+#pragma unroll 4
                 for (int kx = kx0; kx <= N; kx += KSTEP, dst += dstep) {
                     const int k = kx >> 1;
                     const float2 zk = zp[k];
