@@ -433,7 +433,14 @@ constexpr int kZ2TrStr = 17;                   // transpose area row stride
 constexpr int kZ2TrWarp = 2 * 16 * kZ2TrStr;   // complex values of a warp's transpose area
 constexpr int kZ2MaxNz = 128;
 constexpr int kZ2Stage = kZ2MaxNz * kZ2Str;    // complex values of one staging tile
-constexpr size_t kZ2Smem = (size_t)(256 + kZ2Warps * kZ2TrWarp + 2 * kZ2Stage) * sizeof(float2);
+// spectra of one component for the tile's columns, one row of Pz/2 + 1 = 129
+// values per column (both mirror halves of kz read the same row), two
+// components in flight
+constexpr int kZ2SpS = 145;                    // floats per staged spectra row (129 used)
+constexpr int kZ2Spec = kZ2Ti * kZ2SpS;        // floats of one component's staged spectra
+constexpr size_t kZ2Smem = (size_t)(256 + kZ2Warps * kZ2TrWarp + 2 * kZ2Stage) * sizeof(float2) +
+                           (size_t)2 * kZ2Spec * sizeof(float);
+static_assert(kZ2Threads == 16 * kZ2Ti, "sixteen threads stage each spectra row");
 
 // 16-point DFT in registers, radix-2 decimation in frequency: natural order
 // in, u[j] = X[bitrev4(j)] out.  HALF: u[8..15] are zero on entry.  LOW:
@@ -473,8 +480,7 @@ __global__ void __launch_bounds__(kZ2Threads, 16 / kZ2Warps)
     const int ky0 = blockIdx.x * kZ2Ti, kx = blockIdx.y;
     const int nz = a.nz, py = a.py;
     const int ci = 2 * warp + col, ky = ky0 + ci;
-    const bool kyok = ky < py, fy = ky > py / 2;
-    const int jy = !kyok ? 0 : (fy ? py - ky : ky);
+    const bool fy = ky > py / 2;
 
     for (int e = tid; e < 256; e += kZ2Threads) tab[e] = tw[((e >> 4) * (e & 15)) << a.tw_shift];
 
@@ -550,10 +556,31 @@ __global__ void __launch_bounds__(kZ2Threads, 16 / kZ2Warps)
     };
     // spectrum of slot c at (ky, kz = q + 16 bitrev4(j)) as the real v with
     // S = v or S = i v
-    const float* spec_lane = spec3 + ((size_t)kx * a.jyc + jy) * a.jzc;  // slot 0
+    // Spectra come into shared memory by per-thread asynchronous copies one
+    // component ahead: thread tid stages row sr = tid / 16 (column ky0 + sr)
+    // at jz = tid % 16 + 16 m; a row beyond py is zero-filled.
+    float* specb = reinterpret_cast<float*>(stage + 2 * kZ2Stage);  // two [kZ2Ti][kZ2SpS]
+    const int sr = tid >> 4, sz = tid & 15;
+    const int sky = ky0 + sr;
+    const bool s_ok = sky < py;
+    const float* spec_row = spec3 + ((size_t)kx * a.jyc + (!s_ok ? 0 : (sky > py / 2 ? py - sky : sky))) * a.jzc;
     const size_t spec_slot = (size_t)a.kx_count * a.jyc * a.jzc;
-    auto load_spec = [&](int c, float (&v)[16]) {
-        const float* base = spec_lane + c * spec_slot;
+    auto issue_spec = [&](int c, float* sb) {
+        const float* src = spec_row + c * spec_slot + sz;
+        uint32_t dst = smem_u32(sb + sr * kZ2SpS + sz);
+        const uint32_t nb = s_ok ? 4u : 0u;
+#pragma unroll
+        for (int m = 0; m < 9; ++m) {
+            if (m < 8 || sz == 0)  // jz = sz + 16 m <= 128
+                asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;" ::"r"(dst + 64u * m), "l"(src + 16 * m),
+                             "r"(nb)
+                             : "memory");
+        }
+        async8_commit();
+    };
+    // spectrum of slot c at (ky, kz = q + 16 bitrev4(j)) from staged row ci
+    auto load_spec = [&](int c, const float* sb, float (&v)[16]) {
+        const float* row = sb + ci * kZ2SpS;
         // the sign of S(ky, kz) against the stored value: flipped by the
         // y parity for ky > Py/2 and by the w parity for kz > Pz/2
         const bool s_lo = fy && ((a.oddv_mask >> c) & 1u);
@@ -562,20 +589,25 @@ __global__ void __launch_bounds__(kZ2Threads, 16 / kZ2Warps)
         for (int j = 0; j < 16; ++j) {
             const int kz = q + 16 * bitrev4(j);
             const bool fz = kz > 128;
-            const float val = kyok ? __ldg(base + (fz ? 256 - kz : kz)) : 0.f;
+            const float val = row[fz ? 256 - kz : kz];
             v[j] = (fz ? s_hi : s_lo) ? -val : val;
         }
     };
 
     if constexpr (!ADJ) {
         float2* st_in = stage + kZ2Stage;
+        issue_spec(0, specb);
         load_tile(st_in, in + (size_t)kx * nz * py);
-        __syncthreads();  // the tile and the twiddle table are in place
+        async8_wait_all();
+        __syncthreads();  // the tile, component 0's spectra and the twiddle table are in place
         float2 X[16];
         fwd_fft(st_in, X);
-        float v[16];
-        load_spec(0, v);
         for (int c = 0; c < a.ncomp; ++c) {
+            // the other spectra buffer was last read by component c - 1,
+            // before the previous barrier
+            if (c + 1 < a.ncomp) issue_spec(c + 1, specb + ((c + 1) & 1) * kZ2Spec);
+            float v[16];
+            load_spec(c, specb + (c & 1) * kZ2Spec, v);
             float2 g[16];
             if ((a.imag3_mask >> c) & 1u) {  // S = i v
 #pragma unroll
@@ -584,13 +616,13 @@ __global__ void __launch_bounds__(kZ2Threads, 16 / kZ2Warps)
 #pragma unroll
                 for (int j = 0; j < 16; ++j) g[j] = make_float2(v[j] * X[j].x, v[j] * X[j].y);
             }
-            if (c + 1 < a.ncomp) load_spec(c + 1, v);  // in flight during the transform
             inv_fft(g);
             // staging tile c % 2: its last reader (the store of component
             // c - 2, or the input read for c = 1) finished before the
             // previous barrier
             float2* st = stage + (c & 1) * kZ2Stage;
             put_stations(st, g);
+            async8_wait_all();  // component c + 1's spectra, visible after the barrier
             __syncthreads();
             store_tile(st, out + ((size_t)kx * a.ncomp + c) * nz * py);
         }
@@ -601,18 +633,21 @@ __global__ void __launch_bounds__(kZ2Threads, 16 / kZ2Warps)
         // component c's tile is copied into staging tile c % 2 while
         // component c - 1 is transformed
         issue_tile(stage, in + (size_t)kx * a.ncomp * nz * py);
+        issue_spec(0, specb);
         for (int c = 0; c < a.ncomp; ++c) {
             float2* st = stage + (c & 1) * kZ2Stage;
-            float v[16];
-            load_spec(c, v);
             async8_wait_all();
-            // tile c has landed everywhere, and every read of tile c - 1
-            // (staging tile (c + 1) % 2) is done
+            // tile c and its spectra have landed everywhere, and every read of
+            // tile c - 1 and its spectra (the other buffers) is done
             __syncthreads();
-            if (c + 1 < a.ncomp)
+            if (c + 1 < a.ncomp) {
                 issue_tile(stage + ((c + 1) & 1) * kZ2Stage, in + ((size_t)kx * a.ncomp + c + 1) * nz * py);
+                issue_spec(c + 1, specb + ((c + 1) & 1) * kZ2Spec);
+            }
             float2 f[16];
             fwd_fft(st, f);
+            float v[16];
+            load_spec(c, specb + (c & 1) * kZ2Spec, v);
             if ((a.imag3_mask >> c) & 1u) {  // conj(S) f with S = i v
 #pragma unroll
                 for (int j = 0; j < 16; ++j) acc[j] = make_float2(acc[j].x + v[j] * f[j].y, acc[j].y - v[j] * f[j].x);
