@@ -253,15 +253,23 @@ __global__ void __launch_bounds__(kYwThreads, 2)
 #pragma unroll
         for (int j = 0; j < 32; ++j) tr[lane + 32 * bitrev5(j)] = u[j];
         __syncthreads();  // E and W^-m O of all four rows are in place
-        for (int e = tid; e < ybs * kYwRows * 8; e += kYwThreads) {
-            const int slot = e & 7, s = (e >> 3) & (kYwRows - 1), yb = e / (8 * kYwRows);
+        {
+            // thread tid writes slot tid % 8 of row kx0 + (tid / 8) % 4 in the
+            // blocks yb = tid / 32, tid / 32 + 8, ...: only yb moves
+            constexpr int YBSTEP = kYwThreads / (8 * kYwRows);
+            const int slot = tid & 7, s = (tid >> 3) & (kYwRows - 1);
             const int kxs = kx0 + s;
-            if (kxs >= kx_count) continue;
-            const int jj = ((slot >> 1) - (kxs >> 1)) & 3;  // the row pair at this 16-byte position
-            const int y = 8 * yb + 2 * jj + (slot & 1);
-            float2 z = make_float2(0.f, 0.f);
-            if (y < ny) z = cadd(areas[2 * s * kYwArea + y], areas[(2 * s + 1) * kYwArea + y]);
-            out[(((size_t)r * ybs + yb) * kx_count + kxs) * 8 + slot] = z;
+            if (kxs < kx_count) {
+                const int jj = ((slot >> 1) - (kxs >> 1)) & 3;  // the row pair at this 16-byte position
+                const float2* ea = areas + 2 * s * kYwArea;
+                const float2* eb = ea + kYwArea;
+                int yb = tid / (8 * kYwRows);
+                int y = 8 * yb + 2 * jj + (slot & 1);
+                float2* dst = out + (((size_t)r * ybs + yb) * kx_count + kxs) * 8 + slot;
+                const size_t dstep = (size_t)YBSTEP * kx_count * 8;
+                for (; yb < ybs; yb += YBSTEP, y += 8 * YBSTEP, dst += dstep)
+                    *dst = y < ny ? cadd(ea[y], eb[y]) : make_float2(0.f, 0.f);
+            }
         }
         __syncthreads();  // the areas are rewritten by the next group
     }
