@@ -37,6 +37,12 @@
 //   E  x: inverse row transforms (C2R, row_c2r)           -> out[c][t][y][x]
 // The adjoint runs the same passes from r[c][t][y][x], multiplies by the
 // conjugate spectra and sums over components in pass C (the transpose).
+// Generic block-FFT kernels serve every size; FP32 plans at the common sizes
+// take register-resident kernels instead: pass C for Pz = 256
+// (vol_z256_kernel), passes B and D for Py = 2048 (vol_yfwd2048_kernel,
+// vol_yinv2048_tiled_kernel) and, with Px = 2048, D writes the tiled layout
+// V[c t][y / 8][kx][8] that pass E reads by bulk copies
+// (launch_row_c2r_tiled).
 #include <algorithm>
 #include <new>
 #include <type_traits>
