@@ -181,10 +181,12 @@ __global__ void __maxnreg__(AwShape::REGS)
         // ---------------- FFT warp f: inverse transforms of layers f, f + 8, ... ----------------
         const int f = warp - J / 32;
         cta_sync();
+        // ring slot of layer n (n % dz) and the parity of n / dz, stepped with
+        // n (n advances by FW < dz)
+        int sz = f, wrap = 0;
         for (int n = f; n < nz; n += FW) {
-            const int sz = n % L.dz;
             int ok = 1;
-            if (lane == 0) ok = ws_wait(&zfull[sz], (uint32_t)((n / L.dz) & 1), abort);
+            if (lane == 0) ok = ws_wait(&zfull[sz], (uint32_t)(wrap & 1), abort);
             ok = __shfl_sync(0xffffffffu, ok, 0);
             if (!ok) {
                 failed = true;
@@ -233,6 +235,11 @@ __global__ void __maxnreg__(AwShape::REGS)
                         dst[y] = v;
                     }
                 }
+            }
+            sz += FW;
+            if (sz >= L.dz) {
+                sz -= L.dz;
+                ++wrap;
             }
         }
         if (a.z_tiled && lane == 0) bulk_wait_all();  // every tensor store has landed
